@@ -1,0 +1,199 @@
+/*
+ * logan.h -- C ABI of a GB300-native (sm_103a) batched X-drop seed-extension
+ * library, after LOGAN (Zeni et al., "LOGAN: High-Performance GPU-Based
+ * X-Drop Long-Read Alignment").
+ *
+ * The operation (paper Sec. III-A, Algorithms 1 and 2, Sec. IV-B): for each
+ * seeded pair of DNA sequences, extend the seed to the right and to the left
+ * with an anti-diagonal dynamic program under linear gap scoring, keep the
+ * running best score, drop cells that fall more than X below it, trim the
+ * band to its live cells, and stop when an anti-diagonal has no live cell.
+ * The pair's result is left best + seed score + right best with the
+ * alignment's begin/end coordinates.
+ *
+ * Semantics fixed where the paper is silent (the same in every entry point):
+ *   - scores are signed values that are ADDED: match > 0 rewards, mismatch
+ *     and gap <= 0 penalise;
+ *   - S(0,0) = 0 and the running best starts at 0, so a side's best is >= 0;
+ *   - anti-diagonal d is pruned against the best of anti-diagonals < d, with
+ *     strict comparison (S < best - X is dropped);
+ *   - the next anti-diagonal covers [first live, last live + 1] of the current
+ *     one, clipped to the matrix; the sweep runs until an anti-diagonal has
+ *     no live cell or its range is empty;
+ *   - the best cell is the first anti-diagonal that reaches the best score,
+ *     smallest row index (bases of A) on it;
+ *   - computed cells = every cell of every evaluated anti-diagonal range
+ *     (d >= 1), including pruned cells and the final all-pruned range.
+ *
+ * Conventions:
+ *   - Every function returns LOGAN_OK (0) or a negative LOGAN_E* code.
+ *   - Pointers marked "device" must point to device memory of the context's
+ *     GPU; all caller memory stays owned by the caller.
+ *   - Batch calls are asynchronous on `stream` (a cudaStream_t; NULL = the
+ *     legacy default stream). Results are valid once the stream is
+ *     synchronised. Argument errors are reported synchronously; per-pair
+ *     input errors are reported in logan_result_t.status.
+ *   - A context is bound to one GPU and must not be used by two host threads
+ *     at once.
+ */
+#ifndef LOGAN_H
+#define LOGAN_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+#define LOGAN_ABI_VERSION 1
+
+/* return / status codes */
+#define LOGAN_OK         0
+#define LOGAN_EINVAL   (-22)  /* invalid argument or invalid pair input */
+#define LOGAN_ENOMEM   (-12)  /* workspace too small / host allocation failed */
+#define LOGAN_EAGAIN   (-11)  /* serving: request exceeds the free budget now */
+#define LOGAN_ECUDA    (-5)   /* a CUDA runtime call failed */
+#define LOGAN_ETIMEOUT (-110) /* a bounded wait expired */
+#define LOGAN_ECANCELED (-125)/* serving: request was cancelled */
+#define LOGAN_ERANGE   (-34)  /* a band outgrew the widest supported window */
+#define LOGAN_ENOTFOUND (-2)  /* serving: unknown ticket */
+
+typedef struct logan_ctx logan_ctx_t;
+
+/*
+ * A pool of sequences in device memory.
+ *   bases:      packed2bit == 0: uint8 ASCII bases 'A','C','G','T' (any other
+ *               byte makes every pair that uses the sequence LOGAN_EINVAL);
+ *               packed2bit == 1: uint32 words, 16 bases per word, base k of
+ *               the pool in word k/16 at bits 2*(k%16)..+1, codes A0 C1 G2 T3.
+ *               The buffer must hold ceil(pool_bases/16)+1 words.
+ *   offsets:    uint64 per sequence, first base of the sequence in the pool.
+ *   lengths:    uint32 per sequence (< 2^31).
+ *   count:      number of sequences.
+ *   pool_bases: number of bases in `bases` (every sequence must lie inside).
+ * Sequences may overlap or share bases; seqsA and seqsB may be the same pool.
+ */
+typedef struct {
+    const void *bases;
+    const uint64_t *offsets;
+    const uint32_t *lengths;
+    uint32_t count;
+    uint32_t packed2bit;
+    uint64_t pool_bases;
+} logan_seqs_t;
+
+/* One seeded pair (device array of n_pairs): sequence idxA of pool A and
+ * idxB of pool B share an exact-or-not seed of `len` bases starting at posA
+ * in A and posB in B. Paper Sec. IV-B: the seed splits the pair into a left
+ * and a right extension. */
+typedef struct {
+    uint32_t idxA, idxB, posA, posB, len;
+} logan_seed_t;
+
+/* Per-pair result (device array of n_pairs, written by the library).
+ *   score  = left + seed score + right (seed score: match/mismatch summed
+ *            over the len seed columns)
+ *   left, right: best score of each extension (>= 0)
+ *   begA/begB: first aligned base in A/B; endA/endB: one past the last
+ *   cells: computed cells of both extensions
+ *   status: LOGAN_OK, LOGAN_EINVAL (bad base, seed outside a sequence, index
+ *           out of range, per-pair X outside [0, 2^29], or
+ *           max(|match|,|mismatch|,|gap|)*(lenA+lenB)+X >= 2^29), or
+ *           LOGAN_ERANGE (a band wider than the fallback window).
+ *   When status != LOGAN_OK every other field is 0. */
+typedef struct {
+    int32_t score;
+    int32_t left;
+    int32_t right;
+    int32_t status;
+    uint32_t begA, begB, endA, endB;
+    uint64_t cells;
+} logan_result_t;
+
+/* Library version string and message for a LOGAN_E* code. */
+const char *logan_version(void);
+const char *logan_strerror(int code);
+
+/* Create a context on CUDA device `device`. `autotune_json` (nullable) is a
+ * table written by logan_autotune_save. The context allocates host memory
+ * only. */
+int logan_ctx_create(logan_ctx_t **ctx, int device, const char *autotune_json);
+void logan_ctx_destroy(logan_ctx_t *ctx);
+
+/* Device workspace needed by logan_extend_batch / logan_extend_batch_plain
+ * for this batch shape: pools A and B (B may equal A) and n_pairs pairs.
+ * Writes the byte count to *bytes. The same workspace can be reused by later
+ * calls on the same stream. */
+int logan_workspace_size(const logan_ctx_t *ctx, const logan_seqs_t *seqsA,
+                         const logan_seqs_t *seqsB, uint32_t n_pairs, size_t *bytes);
+
+/*
+ * Batched X-drop seed extension, persistent length-binned form.
+ *   match/mismatch/gap: added scores, |v| <= 1000, gap <= 0, mismatch <= match.
+ *   X: drop threshold for every pair, 0 <= X <= 2^29; X_per_pair (nullable,
+ *      device int32[n_pairs]) overrides it per pair.
+ *   workspace: device buffer of >= logan_workspace_size bytes, 256-aligned.
+ *   out: device logan_result_t[n_pairs].
+ * Pipeline on `stream`: pack (ASCII input only) -> split + seed score ->
+ * length/X binning -> persistent extension kernels (one per band-width
+ * class, widest last, longest items first) -> combine. With graphs enabled
+ * (logan_set_option) the launch sequence is captured once per shape and
+ * replayed. Returns LOGAN_EINVAL for invalid scalars or pointers,
+ * LOGAN_ENOMEM if ws_bytes is too small, LOGAN_ECUDA on a launch failure.
+ */
+int logan_extend_batch(logan_ctx_t *ctx, const logan_seqs_t *seqsA, const logan_seqs_t *seqsB,
+                       const logan_seed_t *seeds, uint32_t n_pairs,
+                       int32_t match, int32_t mismatch, int32_t gap,
+                       int32_t X, const int32_t *X_per_pair,
+                       void *workspace, size_t ws_bytes,
+                       logan_result_t *out, void *stream);
+
+/* Same operation and results, one-launch-per-batch baseline form (the
+ * paper's Sec. IV-B inter-sequence scheme): one warp per extension in input
+ * order, no binning and no persistence; bands that outgrow its window go to
+ * the same wider fallbacks. */
+int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
+                             const logan_seqs_t *seqsB, const logan_seed_t *seeds,
+                             uint32_t n_pairs, int32_t match, int32_t mismatch, int32_t gap,
+                             int32_t X, const int32_t *X_per_pair,
+                             void *workspace, size_t ws_bytes,
+                             logan_result_t *out, void *stream);
+
+/* Options (logan_set_option / logan_get_option):
+ *   LOGAN_OPT_GRAPHS        1: capture + replay CUDA graphs (default 0)
+ *   LOGAN_OPT_TIMING        1: record CUDA events around the extension
+ *                           kernels; read back with logan_last_timing
+ *   LOGAN_OPT_FORCE_LEVEL   -1: autotuned (default); k >= 0: start every
+ *                           extension at window level k (testing aid)
+ *   LOGAN_OPT_MAX_LEVEL     highest register-window level used before the
+ *                           global-memory fallback (default: all)
+ *   LOGAN_OPT_RING_CAP      log2 of the fallback window in cells (10..22,
+ *                           default 16); changes the workspace size
+ *   LOGAN_OPT_PLAIN_LEVEL   window level of the plain form (default 1)
+ */
+#define LOGAN_OPT_GRAPHS 1
+#define LOGAN_OPT_TIMING 2
+#define LOGAN_OPT_FORCE_LEVEL 3
+#define LOGAN_OPT_MAX_LEVEL 4
+#define LOGAN_OPT_RING_CAP 5
+#define LOGAN_OPT_PLAIN_LEVEL 6
+int logan_set_option(logan_ctx_t *ctx, int option, int64_t value);
+int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
+
+/* Number of window levels and the window width (cells) / threads of level k. */
+int logan_num_levels(void);
+int logan_level_info(int level, int *window_cells, int *threads_per_unit);
+
+/* Timing of the last batch call made with LOGAN_OPT_TIMING = 1 (synchronises
+ * the stream of that call): ms[k] = device time of extension level k
+ * (k < logan_num_levels()), ms[levels] = the global fallback, and
+ * ms[levels+1] = the whole pipeline. `n` = capacity of ms. Also returns the
+ * number of extension items that started at, or escalated into, each level
+ * in items[] (nullable, same layout). */
+int logan_last_timing(logan_ctx_t *ctx, float *ms, uint32_t *items, int n);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* LOGAN_H */

@@ -1,0 +1,139 @@
+"""CPU oracle for batched X-drop seed extension -- TEST INFRASTRUCTURE ONLY.
+
+Loads ``xdrop_oracle.c`` (compiled with the host C compiler into
+``oracle/_build/liboracle.so``) through ctypes.  Only the tests, the smoke
+check and the CPU-baseline leg of ``bench.py`` may use it; the library and
+its Python binding never import it.  It shares no code with the CUDA path.
+
+Every function follows the passages and readings listed at the top of
+``xdrop_oracle.c``.  Parity status: pinned (brute-force full DP at X = inf,
+closed forms, invariants and hand-derived worked examples in tests/).
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import subprocess
+from typing import Optional
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+_SRC = os.path.join(_HERE, "xdrop_oracle.c")
+_BUILD = os.path.join(_HERE, "_build")
+_LIB_PATH = os.path.join(_BUILD, "liboracle.so")
+
+OK, INVALID, NOMEM = 0, 1, 2
+
+PAIR_DTYPE = np.dtype([("score", "<i8"), ("left", "<i8"), ("right", "<i8"),
+                       ("begA", "<i8"), ("begB", "<i8"), ("endA", "<i8"),
+                       ("endB", "<i8"), ("cells", "<i8"), ("status", "<i8")])
+
+
+class _Ext(ctypes.Structure):
+    _fields_ = [("best", ctypes.c_int64), ("bi", ctypes.c_int64),
+                ("bj", ctypes.c_int64), ("cells", ctypes.c_int64)]
+
+
+def build(force: bool = False) -> str:
+    """Compile the oracle with the host C compiler (gcc -O2, no -march flags)."""
+    os.makedirs(_BUILD, exist_ok=True)
+    if force or not os.path.exists(_LIB_PATH) or \
+            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+        tmp = _LIB_PATH + f".{os.getpid()}.tmp"
+        subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
+                               "-o", tmp, _SRC])
+        os.replace(tmp, _LIB_PATH)
+    return _LIB_PATH
+
+
+_lib = None
+
+
+def lib():
+    global _lib
+    if _lib is None:
+        L = ctypes.CDLL(build())
+        i64, p = ctypes.c_int64, ctypes.c_void_p
+        L.oracle_xdrop_extend.argtypes = [p, i64, p, i64, i64, i64, i64, i64,
+                                          ctypes.POINTER(_Ext)]
+        L.oracle_xdrop_extend.restype = ctypes.c_int
+        L.oracle_pair.argtypes = [p, i64, p, i64, i64, i64, i64, i64, i64, i64, i64, p]
+        L.oracle_pair.restype = ctypes.c_int
+        L.oracle_batch.argtypes = [p, p, p, ctypes.c_uint32, p, p, p, ctypes.c_uint32,
+                                   p, i64, i64, i64, i64, i64, p, ctypes.c_int, p]
+        L.oracle_batch.restype = ctypes.c_int
+        L.oracle_params_valid.argtypes = [i64, i64, i64, i64]
+        L.oracle_params_valid.restype = ctypes.c_int
+        _lib = L
+    return _lib
+
+
+def _buf(x: bytes):
+    return ctypes.c_char_p(x) if x else ctypes.c_char_p(b"")
+
+
+def extend(a: bytes, b: bytes, match: int = 1, mismatch: int = -1, gap: int = -1,
+           X: int = 50):
+    """One X-drop extension of a against b (both read forwards from cell (0,0)).
+
+    Returns (best, bi, bj, cells): best score >= 0, the number of bases of a and
+    b consumed at the best cell, and the computed-cell count.
+    """
+    out = _Ext()
+    rc = lib().oracle_xdrop_extend(_buf(a), len(a), _buf(b), len(b), match, mismatch,
+                                   gap, X, ctypes.byref(out))
+    if rc:
+        raise MemoryError("oracle extension could not allocate")
+    return out.best, out.bi, out.bj, out.cells
+
+
+def pair(A: bytes, B: bytes, posA: int, posB: int, k: int, match: int = 1,
+         mismatch: int = -1, gap: int = -1, X: int = 50) -> np.void:
+    """One seeded pair: left extension + seed + right extension (PAIR_DTYPE)."""
+    r = np.zeros(1, dtype=PAIR_DTYPE)
+    lib().oracle_pair(_buf(A), len(A), _buf(B), len(B), posA, posB, k, match, mismatch,
+                      gap, X, r.ctypes.data)
+    return r[0]
+
+
+def params_valid(match: int, mismatch: int, gap: int, X: int) -> bool:
+    return bool(lib().oracle_params_valid(match, mismatch, gap, X))
+
+
+def batch(poolA: np.ndarray, offA: np.ndarray, lenA: np.ndarray,
+          poolB: np.ndarray, offB: np.ndarray, lenB: np.ndarray,
+          seeds: np.ndarray, match: int, mismatch: int, gap: int, X: int,
+          Xs: Optional[np.ndarray] = None, threads: Optional[int] = None):
+    """Every pair of a batch, one pair per task over `threads` host threads.
+
+    seeds: structured array of (idxA, idxB, posA, posB, len) uint32 records.
+    Returns (results as PAIR_DTYPE array, threads used).
+    """
+    poolA = np.ascontiguousarray(poolA, dtype=np.uint8)
+    poolB = np.ascontiguousarray(poolB, dtype=np.uint8)
+    offA = np.ascontiguousarray(offA, dtype=np.uint64)
+    offB = np.ascontiguousarray(offB, dtype=np.uint64)
+    lenA = np.ascontiguousarray(lenA, dtype=np.uint32)
+    lenB = np.ascontiguousarray(lenB, dtype=np.uint32)
+    sd = np.ascontiguousarray(
+        np.stack([seeds[f] for f in ("idxA", "idxB", "posA", "posB", "len")], axis=1)
+        .astype(np.uint32))
+    n = sd.shape[0]
+    out = np.zeros(n, dtype=PAIR_DTYPE)
+    xs = None if Xs is None else np.ascontiguousarray(Xs, dtype=np.int32)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    used = lib().oracle_batch(poolA.ctypes.data, offA.ctypes.data, lenA.ctypes.data,
+                              lenA.size, poolB.ctypes.data, offB.ctypes.data,
+                              lenB.ctypes.data, lenB.size, sd.ctypes.data, n,
+                              match, mismatch, gap, X,
+                              None if xs is None else xs.ctypes.data, int(threads),
+                              out.ctypes.data)
+    return out, used
+
+
+def run_batch(b, threads: Optional[int] = None):
+    """Convenience wrapper for a synth.Batch-like object."""
+    return batch(b.poolA, b.offA, b.lenA, b.poolB, b.offB, b.lenB, b.seeds, b.match,
+                 b.mismatch, b.gap, b.X, b.Xs, threads)
