@@ -1,0 +1,336 @@
+#!/usr/bin/env python
+"""Benchmark: batched X-drop seed extension on GB300.
+
+Workload (default): 100,000 seeded pairs, lognormal lengths (median 10 kbp,
+sigma 0.5, clipped to 1-30 kbp), 80 % related at 12 % error with a
+midpoint 17-mer seed, 20 % unrelated with one planted shared 17-mer,
+X = 100, +1/-1/-1, 2-bit packed input, int32 scores.  Synthetic, seeded.
+
+One step = one pass of the whole pipeline over the batch through the C ABI
+(logan_extend_batch: validate, split + seed score, binning, persistent
+extension kernels, fallback, combine) with the inputs resident in HBM.
+The packed pools (~0.55 GB) are larger than L2 (129 MB), so no flush is
+needed between steps.
+
+Prints ONE JSON line (rank 0).  Metric: GCUPS over the cells the X-drop
+computes (every evaluated cell of every anti-diagonal range).
+
+--impl reference times the CPU oracle on the host cores instead (a bounded
+sample of the same workload per step).
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+METRIC = "X-drop GCUPS (computed cells), batched vs plain launch; serving p50/p99 ms"
+OPS_PER_CELL = 8          # Algorithm 2 per cell: compare, add, 2 gap adds, 2 max, X-drop compare, select
+LANES_PER_SM = 128        # 4 sub-partitions x 32 integer lanes per clock (Blackwell SM)
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=5)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--pairs", type=int, default=100_000)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0,
+                    help="target host time of the oracle sample")
+    ap.add_argument("--kernel-only", action="store_true",
+                    help="only the timed persistent steps (for profiler runs)")
+    return ap.parse_args()
+
+
+def workload(pairs: int, rank: int):
+    from paper_2002_05200_gb300 import synth
+    b = synth.lognormal_batch(n_pairs=pairs, seed=2 + 1000 * rank)
+    b.meta["packed2bit"] = True
+    return b
+
+
+def workload_config(b, pairs):
+    return {"workload": "lognormal_batch", "pairs": pairs, "median_len": 10_000,
+            "len_sigma": 0.5, "len_clip": [1000, 30000], "related_frac": 0.8,
+            "error_rate": 0.12, "seed_len": 17, "X": 100, "scoring": [1, -1, -1],
+            "input": "2-bit packed", "l2": "inputs larger than L2 (packed pools "
+            f"{(b.poolA.size + b.poolB.size) // 4 / 1e6:.0f} MB), no flush",
+            "parallelism": "replicas (independent pairs per GPU, no collective)"}
+
+
+# ---------------------------------------------------------------- clocks
+class ClockSampler:
+    """nvidia-smi sampling of SM clocks and throttle reasons during a region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+         "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+         "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.lines = []
+
+    def __enter__(self):
+        try:
+            self.proc = subprocess.Popen(["nvidia-smi", f"--id={self.index}", f"--query-gpu={self.Q}",
+                                          "--format=csv,noheader,nounits", "-lms", "200"],
+                                         stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.t = threading.Thread(target=self._read, daemon=True)
+            self.t.start()
+        except (OSError, FileNotFoundError):
+            self.proc = None
+        return self
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def __exit__(self, *a):
+        if self.proc:
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self):
+        sm, mx, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for ln in self.lines:
+            f = [x.strip() for x in ln.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1]))
+                mx = float(f[2])
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        if not sm:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        return {"sm_mhz": statistics.median(sm), "sm_max_mhz": mx, "reasons": sorted(reasons),
+                "samples": len(sm)}
+
+
+# ---------------------------------------------------------------- CPU oracle
+def cpu_sample(b, seconds: float, threads=None):
+    """Times the oracle on consecutive chunks of pairs until `seconds` of host
+    time are spent (at least one chunk).  Returns (GCUPS, cores, pairs, cells, s)."""
+    import oracle
+    threads = threads or os.cpu_count() or 1
+    chunk = max(threads * 4, 64)
+    done, cells, t0 = 0, 0, time.perf_counter()
+    while done < b.n_pairs:
+        sub = b.subset(np.arange(done, min(done + chunk, b.n_pairs)))
+        res, used = oracle.run_batch(sub, threads)
+        cells += int(res["cells"][res["status"] == 0].sum())
+        done += sub.n_pairs
+        if time.perf_counter() - t0 >= seconds:
+            break
+    dt = time.perf_counter() - t0
+    return cells / dt / 1e9, used, done, cells, dt
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    b = workload(args.pairs, 0)
+    per_step = max(1.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
+    for _ in range(args.warmup):
+        cpu_sample(b, per_step / 4)
+    vals, cores, pairs, secs = [], 0, 0, 0.0
+    for _ in range(args.steps):
+        g, cores, pairs, cells, dt = cpu_sample(b, per_step)
+        vals.append(g)
+        secs += dt
+    value = float(np.mean(vals))
+    sample = (f"first {pairs} of {b.n_pairs} pairs per step (~{per_step:.0f} s of host time), "
+              "all host cores, one pair per task")
+    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+            "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "int64", "data": "synthetic",
+            "config": workload_config(b, args.pairs),
+            "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                    "d2h_bytes_per_step": 0}}
+    print(json.dumps(line), flush=True)
+
+
+# ---------------------------------------------------------------- GPU arm
+def main():
+    args = parse()
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    if args.impl == "reference":
+        return run_reference(args, rank, world)
+
+    import torch
+    import torch.distributed as dist
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+
+    from paper_2002_05200_gb300 import build as lib_build, logan
+    lib_build.build()
+    b = workload(args.pairs, rank)
+    A, B, S, Xs = logan.batch_to_device(b, packed2bit=True, device=f"cuda:{local}")
+    ctx = logan.Context(local)
+    stream = torch.cuda.Stream()
+    ws = ctx.workspace(A, B, b.n_pairs)
+    out = torch.empty((b.n_pairs, 10), dtype=torch.int32, device=f"cuda:{local}")
+
+    def barrier():
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    def step(plain=False):
+        ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, workspace=ws, out=out,
+                   stream=stream, plain=plain)
+
+    def timed(fn, steps, warmup):
+        with torch.cuda.stream(stream):
+            for _ in range(warmup):
+                fn()
+        barrier()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(steps):
+            fn()
+        e1.record(stream)
+        e1.synchronize()
+        barrier()
+        ms = e0.elapsed_time(e1)
+        if world > 1:
+            t = torch.tensor([ms], device=f"cuda:{local}")
+            dist.all_reduce(t, op=dist.ReduceOp.MAX)
+            ms = float(t.item())
+        return ms / steps
+
+    # persistent form, with per-level events kept for every timed step
+    ctx.set_option(logan.OPT_TIMING, 1)
+    ctx.set_option(logan.OPT_GRAPHS, 0)
+    with ClockSampler(local) as clk:
+        ms = timed(step, args.steps, args.warmup)
+    res = logan.results_to_numpy(out)
+    cells = int(res["cells"].sum())
+    nl = logan.num_levels()
+    per_call = [ctx.last_stats(k) for k in range(min(args.steps, 32))]
+    last = per_call[0]
+    level_ms = np.mean([[c["level_ms"][l] for l in range(nl + 1)] for c in per_call], axis=0)
+    launches = int(last["launches"])
+    # rank totals
+    tot_cells = cells
+    if world > 1:
+        t = torch.tensor([cells], dtype=torch.float64, device=f"cuda:{local}")
+        dist.all_reduce(t)
+        tot_cells = int(t.item())
+    value = tot_cells / (ms * 1e-3) / 1e9
+
+    # dominant kernel: the level with the most device time
+    dom = int(np.argmax(level_ms))
+    dom_cells = int(last["cells"][dom])
+    win, thr = logan.level_info(dom) if dom < nl else (1 << 16, 256)
+    clocks = clk.summary()
+    sm_max = clocks.get("sm_max_mhz") or 2070.0
+    n_sms = torch.cuda.get_device_properties(local).multi_processor_count
+    peak = n_sms * LANES_PER_SM * sm_max * 1e6 / 1e9   # Gop/s
+    achieved = OPS_PER_CELL * dom_cells / (level_ms[dom] * 1e-3) / 1e9 if level_ms[dom] > 0 else 0.0
+
+    line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "dtype": "int32", "data": "synthetic", "config": workload_config(b, args.pairs),
+            "clocks": clocks, "gpu_launches": launches * args.steps,
+            "cells_per_step": tot_cells,
+            "levels": {"ms": [round(float(v), 4) for v in level_ms],
+                       "items": last["items"], "cells": last["cells"]}}
+    line["roofline"] = {
+        "bound": "alu", "kernel": f"window level {dom}" if dom < nl else "ring fallback",
+        "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+        "traffic": None,
+        "ops_per_cell": OPS_PER_CELL, "cells": dom_cells, "launch_ms": float(level_ms[dom]),
+        "peak_basis": f"{n_sms} SMs x {LANES_PER_SM} int lanes x {sm_max:.0f} MHz (recipe unit counts, max clock)"}
+    if args.kernel_only:
+        if rank == 0:
+            print(json.dumps(line), flush=True)
+        return
+
+    ctx.set_option(logan.OPT_TIMING, 0)
+    if not args.no_plain:
+        ms_plain = timed(lambda: step(plain=True), args.steps, 1)
+        resp = logan.results_to_numpy(out)
+        same = bool(np.array_equal(resp, res))
+        line["plain"] = {"value": tot_cells / (ms_plain * 1e-3) / 1e9, "unit": "GCUPS",
+                         "ms_per_step": ms_plain, "results_identical": same}
+
+    if not args.no_e2e:
+        # end to end through the public API: pinned host inputs -> device ->
+        # extend -> results back to pinned host memory, every step
+        hA = {k: v.cpu().pin_memory() for k, v in (("bases", A.bases), ("off", A.offsets),
+                                                   ("len", A.lengths))}
+        hB = {k: v.cpu().pin_memory() for k, v in (("bases", B.bases), ("off", B.offsets),
+                                                   ("len", B.lengths))}
+        hS = S.cpu().pin_memory()
+        hX = Xs.cpu().pin_memory() if Xs is not None else None
+        hout = torch.empty_like(out, device="cpu").pin_memory()
+        dA = logan.DevicePool(torch.empty_like(A.bases), torch.empty_like(A.offsets),
+                              torch.empty_like(A.lengths), True, A.pool_bases)
+        dB = logan.DevicePool(torch.empty_like(B.bases), torch.empty_like(B.offsets),
+                              torch.empty_like(B.lengths), True, B.pool_bases)
+        dS = torch.empty_like(S)
+        h2d = sum(t.numel() * t.element_size() for t in list(hA.values()) + list(hB.values()) + [hS])
+        d2h = hout.numel() * hout.element_size()
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                dA.bases.copy_(hA["bases"], non_blocking=True)
+                dA.offsets.copy_(hA["off"], non_blocking=True)
+                dA.lengths.copy_(hA["len"], non_blocking=True)
+                dB.bases.copy_(hB["bases"], non_blocking=True)
+                dB.offsets.copy_(hB["off"], non_blocking=True)
+                dB.lengths.copy_(hB["len"], non_blocking=True)
+                dS.copy_(hS, non_blocking=True)
+                ctx.extend(dA, dB, dS, b.match, b.mismatch, b.gap, b.X, Xs, workspace=ws,
+                           out=out, stream=stream)
+                hout.copy_(out, non_blocking=True)
+
+        ms_e2e = timed(e2e_step, args.steps, 1)
+        ok = bool(np.array_equal(hout.numpy().view(logan.RESULT_DTYPE).reshape(-1), res))
+        line["e2e"] = {"value": tot_cells / (ms_e2e * 1e-3) / 1e9, "unit": "GCUPS",
+                       "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                       "ms_per_step": ms_e2e, "results_identical": ok}
+
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        g, cores, pairs, ccells, dt = cpu_sample(b, args.cpu_seconds)
+        line["cpu_baseline"] = {"value": g, "unit": "GCUPS", "cores": cores, "kind": "oracle",
+                                "sample": f"first {pairs} of {b.n_pairs} pairs ({ccells} cells, "
+                                          f"{dt:.1f} s), one pair per task on all host cores"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    ctx.close()
+    if world > 1:
+        dist.destroy_process_group()
+
+
+if __name__ == "__main__":
+    main()

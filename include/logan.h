@@ -185,13 +185,46 @@ int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
 int logan_num_levels(void);
 int logan_level_info(int level, int *window_cells, int *threads_per_unit);
 
-/* Timing of the last batch call made with LOGAN_OPT_TIMING = 1 (synchronises
- * the stream of that call): ms[k] = device time of extension level k
- * (k < logan_num_levels()), ms[levels] = the global fallback, and
- * ms[levels+1] = the whole pipeline. `n` = capacity of ms. Also returns the
- * number of extension items that started at, or escalated into, each level
- * in items[] (nullable, same layout). */
-int logan_last_timing(logan_ctx_t *ctx, float *ms, uint32_t *items, int n);
+/* Statistics of the last batch call made with LOGAN_OPT_TIMING = 1 (the
+ * call records CUDA events around every extension level on its stream; this
+ * function synchronises on them and reads the level counters from the
+ * workspace, which must not have been reused since).
+ *   level_ms[k]  device time of window level k (k < logan_num_levels()),
+ *                level_ms[logan_num_levels()] = the global-memory fallback;
+ *   total_ms     the whole pipeline of the call;
+ *   items[k]     extensions that ran at level k (started there or escalated
+ *                into it);
+ *   cells[k]     computed cells of the extensions that completed at level k;
+ *   launches     kernels the call launched. */
+#define LOGAN_MAX_LEVELS 8
+typedef struct {
+    float level_ms[LOGAN_MAX_LEVELS + 1];
+    float total_ms;
+    uint32_t items[LOGAN_MAX_LEVELS + 1];
+    uint64_t cells[LOGAN_MAX_LEVELS + 1];
+    uint32_t launches;
+} logan_stats_t;
+int logan_last_stats(logan_ctx_t *ctx, logan_stats_t *stats);
+/* The same for an earlier timed call: back = 0 is the last one, up to 31.
+ * For back > 0 only the times and `launches` are filled (items/cells are 0:
+ * the counters they come from have been overwritten). */
+int logan_call_stats(logan_ctx_t *ctx, int back, logan_stats_t *stats);
+
+/* Integer-instruction throughput microbenchmark on `device` (the ALU
+ * roofline's measured denominator): every thread of a grid of
+ * (SMs x blocks_per_sm) blocks runs independent chains of `op` (0: 32-bit
+ * add, 1: 32-bit max, 2: fused add+max) for `iters` iterations.  Writes the
+ * achieved thread-instructions per second (one warp instruction = 32) and
+ * the kernel time.  Synchronous; allocates and frees a small device buffer. */
+int logan_intpeak(int device, int op, int iters, double *instr_per_s, float *ms);
+
+/* Start-level table: X class -> first window level of an extension.  X
+ * classes: X <= 15, <= 35, <= 75, <= 150, <= 300, <= 700, <= 2000, larger
+ * (LOGAN_X_CLASSES entries).  logan_autotune fills it by timing every level
+ * on a sample batch; logan_ctx_create reads it back from JSON. */
+#define LOGAN_X_CLASSES 8
+int logan_set_level_table(logan_ctx_t *ctx, const int8_t *levels, int n);
+int logan_get_level_table(const logan_ctx_t *ctx, int8_t *levels, int n);
 
 #ifdef __cplusplus
 }

@@ -1,0 +1,543 @@
+// C ABI of the library (declared in include/logan.h): context, options,
+// workspace layout, and the batch pipeline
+//   [pack] -> validate -> split -> bin -> extension levels -> ring -> combine
+// launched asynchronously on the caller's stream, optionally captured into a
+// CUDA graph per batch shape and replayed.
+#include <algorithm>
+#include <cstdio>
+#include <cstdlib>
+#include <cstring>
+#include <mutex>
+#include <string>
+#include <vector>
+
+#include "internal.h"
+#include "../../include/logan.h"
+
+using namespace logan;
+
+namespace {
+
+constexpr size_t kAlign = 256;
+constexpr int kEvSets = 32;        // timed calls whose events are kept
+constexpr int kEvPerSet = kNumLevels + 4;
+inline size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
+
+struct GraphEntry {
+    std::vector<uint64_t> key;
+    cudaGraphExec_t exec = nullptr;
+    uint64_t last_use = 0;
+};
+
+}  // namespace
+
+struct logan_ctx {
+    int device = 0;
+    int num_sms = 0;
+    int64_t opt_graphs = 0;
+    int64_t opt_timing = 0;
+    int64_t force_level = -1;
+    int64_t max_level = kNumLevels - 1;
+    int64_t ring_log2 = 16;
+    int64_t plain_level = 1;
+    LevelTable table{};
+    int blocks_per_sm[kNumLevels] = {};
+    // timing: the events of the last kEvSets timed calls (ring)
+    cudaEvent_t evs[kEvSets][kEvPerSet] = {};
+    cudaEvent_t* ev = evs[0];      // set of the call in progress / last call
+    uint64_t timed_calls = 0;
+    struct CallInfo {
+        int first_level = 0;
+        int max_level = 0;
+        uint32_t launches = 0;
+        Counters* counters = nullptr;
+    } calls[kEvSets];
+    bool timing_pending = false;
+    uint32_t launches_last = 0;
+    // graph cache
+    std::vector<GraphEntry> graphs;
+    uint64_t use_clock = 0;
+};
+
+namespace {
+
+struct Layout {
+    size_t wordsA = 0, wordsB = 0, badA = 0, badB = 0, items = 0, info = 0, ext = 0, queues = 0,
+           counters = 0, hist = 0, ring = 0, total = 0;
+    bool same = false;
+    uint32_t ring_slots = 0;
+    uint32_t ring_cap = 0;
+};
+
+bool same_pool(const logan_seqs_t* a, const logan_seqs_t* b) {
+    return a->bases == b->bases && a->offsets == b->offsets && a->lengths == b->lengths &&
+           a->count == b->count && a->packed2bit == b->packed2bit && a->pool_bases == b->pool_bases;
+}
+
+size_t words_bytes(const logan_seqs_t* s) {
+    return s->packed2bit ? 0 : ((s->pool_bases + 15) / 16 + 1) * sizeof(uint32_t);
+}
+
+Layout make_layout(const logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B, uint32_t n) {
+    Layout L;
+    L.same = same_pool(A, B);
+    const size_t items = size_t(2) * n;
+    size_t off = 0;
+    auto take = [&](size_t bytes) {
+        const size_t at = off;
+        off += up(bytes);
+        return at;
+    };
+    L.wordsA = take(words_bytes(A));
+    L.wordsB = take(L.same ? 0 : words_bytes(B));
+    L.badA = take(A->count);
+    L.badB = take(L.same ? 0 : B->count);
+    L.items = take(items * sizeof(Item));
+    L.info = take(size_t(n) * sizeof(PairInfo));
+    L.ext = take(items * sizeof(ExtRes));
+    L.queues = take(size_t(kNumLevels + 1) * items * sizeof(uint32_t));
+    L.counters = take(sizeof(Counters));
+    L.hist = take(sizeof(uint32_t) * kNumLevels * kBuckets);
+    L.ring_cap = 1u << c->ring_log2;
+    L.ring_slots = uint32_t(std::max<size_t>(1, std::min<size_t>(size_t(c->num_sms), items)));
+    L.ring = take(size_t(L.ring_slots) * 3 * L.ring_cap * sizeof(int32_t));
+    L.total = off;
+    return L;
+}
+
+bool params_ok(int32_t match, int32_t mismatch, int32_t gap, int32_t X) {
+    auto a = [](int32_t v) { return v < 0 ? -int64_t(v) : int64_t(v); };
+    return a(match) <= kMaxParam && a(mismatch) <= kMaxParam && a(gap) <= kMaxParam && gap <= 0 &&
+           mismatch <= match && X >= 0 && X <= kMaxX;
+}
+
+bool pool_ok(const logan_seqs_t* s) {
+    if (!s || s->packed2bit > 1) return false;
+    if (s->count == 0) return true;
+    return s->bases && s->offsets && s->lengths;
+}
+
+struct DeviceGuard {
+    int prev = -1;
+    explicit DeviceGuard(int dev) {
+        if (cudaGetDevice(&prev) != cudaSuccess) prev = -1;
+        if (prev != dev) cudaSetDevice(dev);
+    }
+    ~DeviceGuard() {
+        int cur = -1;
+        if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+    }
+};
+
+void default_table(LevelTable& t) {
+    // X class -> first window level.  Band width is about 0.8 X on related
+    // reads; a level needs width + cells-per-lane + 1 rows of window.
+    const int8_t lv[kXClasses] = {0, 1, 1, 2, 3, 4, 5, 6};
+    for (int i = 0; i < kXClasses; ++i) t.lv[i] = lv[i];
+    t.max_level = kNumLevels - 1;
+    t.only_xclass = -1;
+}
+
+int launch_level(logan_ctx* c, int level, const KernelArgs& ka, cudaStream_t s) {
+    const int per_sm = std::max(1, c->blocks_per_sm[level]);
+    const int grid = c->num_sms * per_sm;
+    cudaError_t e = level < kWarpLevels ? launch_warp_level_persistent(level, ka, grid, s)
+                                        : launch_cta_level(level, ka, grid, 0, s);
+    return e == cudaSuccess ? LOGAN_OK : LOGAN_ECUDA;
+}
+
+// The whole pipeline on `s` (no synchronisation).  plain != 0: one-launch
+// form at c->plain_level, in input order.
+int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
+                 const logan_seed_t* seeds, uint32_t n_pairs, Scoring sc, int32_t X,
+                 const int32_t* Xs, char* ws, const Layout& L, logan_result_t* out,
+                 cudaStream_t s, int plain, bool timing) {
+    PoolDev pa = {A->bases, A->offsets, A->lengths, A->count, A->packed2bit, A->pool_bases,
+                  A->packed2bit ? static_cast<const uint32_t*>(A->bases)
+                                : reinterpret_cast<const uint32_t*>(ws + L.wordsA),
+                  reinterpret_cast<uint8_t*>(ws + L.badA)};
+    PoolDev pb = pa;
+    if (!L.same) {
+        pb = {B->bases, B->offsets, B->lengths, B->count, B->packed2bit, B->pool_bases,
+              B->packed2bit ? static_cast<const uint32_t*>(B->bases)
+                            : reinterpret_cast<const uint32_t*>(ws + L.wordsB),
+              reinterpret_cast<uint8_t*>(ws + L.badB)};
+    }
+    cudaError_t e = cudaSuccess;
+    uint32_t launches = 0;
+    if (timing) e = cudaEventRecord(c->ev[kNumLevels + 1], s);
+    if (e == cudaSuccess && !A->packed2bit && A->pool_bases) {
+        e = launch_pack(pa, reinterpret_cast<uint32_t*>(ws + L.wordsA), s);
+        ++launches;
+    }
+    if (e == cudaSuccess) e = launch_validate(pa, s);
+    launches += A->count ? 1 : 0;
+    if (!L.same) {
+        if (e == cudaSuccess && !B->packed2bit && B->pool_bases) {
+            e = launch_pack(pb, reinterpret_cast<uint32_t*>(ws + L.wordsB), s);
+            ++launches;
+        }
+        if (e == cudaSuccess) e = launch_validate(pb, s);
+        launches += B->count ? 1 : 0;
+    }
+    Item* items = reinterpret_cast<Item*>(ws + L.items);
+    PairInfo* info = reinterpret_cast<PairInfo*>(ws + L.info);
+    ExtRes* ext = reinterpret_cast<ExtRes*>(ws + L.ext);
+    uint32_t* queues = reinterpret_cast<uint32_t*>(ws + L.queues);
+    Counters* counters = reinterpret_cast<Counters*>(ws + L.counters);
+    const uint32_t n_items = 2u * n_pairs;
+    if (e == cudaSuccess)
+        e = launch_split(pa, pb, seeds, n_pairs, sc, X, Xs, items, info, ext, s);
+    ++launches;
+    const int maxl = int(c->max_level);
+    LevelTable tab = c->table;
+    tab.max_level = maxl;
+    int first = 0;
+    if (e == cudaSuccess) {
+        if (plain) {
+            first = int(std::min<int64_t>(c->plain_level, maxl));
+            e = launch_reset_counters(counters, n_items, first, s);
+            ++launches;
+        } else {
+            const int force = c->force_level >= 0 ? int(std::min<int64_t>(c->force_level, maxl)) : -1;
+            e = launch_bin(items, n_items, tab, force, reinterpret_cast<uint32_t*>(ws + L.hist), queues,
+                           n_items, counters, s);
+            launches += 3;
+        }
+    }
+    if (e != cudaSuccess) return LOGAN_ECUDA;
+    KernelArgs ka;
+    ka.wa = pa.words;
+    ka.wb = pb.words;
+    ka.items = items;
+    ka.ext = ext;
+    ka.queues = queues;
+    ka.counters = counters;
+    ka.ring = reinterpret_cast<int32_t*>(ws + L.ring);
+    ka.qcap = n_items;
+    ka.n_items = n_items;
+    ka.ring_cap = L.ring_cap;
+    ka.n_ring_slots = L.ring_slots;
+    ka.max_level = uint32_t(maxl);
+    ka.sc = sc;
+    for (int lvl = plain ? first : 0; lvl <= maxl; ++lvl) {
+        if (timing && cudaEventRecord(c->ev[lvl], s) != cudaSuccess) return LOGAN_ECUDA;
+        int rc = LOGAN_OK;
+        if (plain && lvl == first) {
+            e = lvl < kWarpLevels ? launch_warp_level_plain(lvl, ka, s)
+                                  : launch_cta_level(lvl, ka, c->num_sms * std::max(1, c->blocks_per_sm[lvl]), 1, s);
+            rc = e == cudaSuccess ? LOGAN_OK : LOGAN_ECUDA;
+        } else {
+            rc = launch_level(c, lvl, ka, s);
+        }
+        if (rc) return rc;
+        ++launches;
+    }
+    // ring fallback: one resident block per ring slot
+    if (timing && cudaEventRecord(c->ev[kNumLevels], s) != cudaSuccess) return LOGAN_ECUDA;
+    if (launch_ring(ka, int(L.ring_slots), s) != cudaSuccess) return LOGAN_ECUDA;
+    if (timing && cudaEventRecord(c->ev[kNumLevels + 2], s) != cudaSuccess) return LOGAN_ECUDA;
+    if (launch_combine(seeds, info, ext, n_pairs, out, s) != cudaSuccess) return LOGAN_ECUDA;
+    launches += 2;  // ring + combine
+    c->launches_last = launches;
+    if (timing) {
+        if (cudaEventRecord(c->ev[kNumLevels + 3], s) != cudaSuccess) return LOGAN_ECUDA;
+        auto& ci = c->calls[c->timed_calls % kEvSets];
+        ci.first_level = plain ? first : 0;
+        ci.max_level = maxl;
+        ci.launches = launches;
+        ci.counters = counters;
+        c->timed_calls += 1;
+        c->timing_pending = true;
+    }
+    return LOGAN_OK;
+}
+
+int extend_common(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
+                  const logan_seed_t* seeds, uint32_t n_pairs, int32_t match, int32_t mismatch,
+                  int32_t gap, int32_t X, const int32_t* Xs, void* ws, size_t ws_bytes,
+                  logan_result_t* out, void* stream, int plain) {
+    if (!c || !pool_ok(A) || !pool_ok(B)) return LOGAN_EINVAL;
+    if (!params_ok(match, mismatch, gap, X)) return LOGAN_EINVAL;
+    if (n_pairs > 0x7fffffffu) return LOGAN_EINVAL;
+    if (n_pairs == 0) return LOGAN_OK;
+    if (!seeds || !out || !ws) return LOGAN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return LOGAN_EINVAL;
+    const Layout L = make_layout(c, A, B, n_pairs);
+    if (ws_bytes < L.total) return LOGAN_ENOMEM;
+    DeviceGuard g(c->device);
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    const Scoring sc = {match, mismatch, gap};
+    const bool timing = c->opt_timing != 0;
+    if (timing) c->ev = c->evs[c->timed_calls % kEvSets];
+    if (!c->opt_graphs || timing || s == nullptr)
+        return run_pipeline(c, A, B, seeds, n_pairs, sc, X, Xs, static_cast<char*>(ws), L, out, s,
+                            plain, timing);
+    // graph path: key = everything the launch sequence depends on
+    std::vector<uint64_t> key = {
+        uint64_t(plain), uint64_t(n_pairs), uint64_t(uint32_t(match)), uint64_t(uint32_t(mismatch)),
+        uint64_t(uint32_t(gap)), uint64_t(uint32_t(X)), uint64_t(uintptr_t(Xs)),
+        uint64_t(uintptr_t(seeds)), uint64_t(uintptr_t(out)), uint64_t(uintptr_t(ws)),
+        uint64_t(uintptr_t(stream)), uint64_t(c->force_level), uint64_t(c->max_level),
+        uint64_t(c->ring_log2), uint64_t(c->plain_level)};
+    for (const logan_seqs_t* p : {A, B}) {
+        key.push_back(uint64_t(uintptr_t(p->bases)));
+        key.push_back(uint64_t(uintptr_t(p->offsets)));
+        key.push_back(uint64_t(uintptr_t(p->lengths)));
+        key.push_back(uint64_t(p->count) | (uint64_t(p->packed2bit) << 32));
+        key.push_back(p->pool_bases);
+    }
+    for (int i = 0; i < kXClasses; ++i) key.push_back(uint64_t(uint8_t(c->table.lv[i])));
+    GraphEntry* hit = nullptr;
+    for (auto& ge : c->graphs)
+        if (ge.key == key) hit = &ge;
+    if (!hit) {
+        cudaGraph_t graph = nullptr;
+        if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
+            return LOGAN_ECUDA;
+        int rc = run_pipeline(c, A, B, seeds, n_pairs, sc, X, Xs, static_cast<char*>(ws), L, out, s,
+                              plain, false);
+        cudaError_t e = cudaStreamEndCapture(s, &graph);
+        if (rc || e != cudaSuccess) {
+            if (graph) cudaGraphDestroy(graph);
+            return rc ? rc : LOGAN_ECUDA;
+        }
+        cudaGraphExec_t exec = nullptr;
+        e = cudaGraphInstantiate(&exec, graph, 0);
+        cudaGraphDestroy(graph);
+        if (e != cudaSuccess) return LOGAN_ECUDA;
+        if (c->graphs.size() >= 8) {
+            auto oldest = c->graphs.begin();
+            for (auto it = c->graphs.begin(); it != c->graphs.end(); ++it)
+                if (it->last_use < oldest->last_use) oldest = it;
+            cudaGraphExecDestroy(oldest->exec);
+            c->graphs.erase(oldest);
+        }
+        c->graphs.push_back(GraphEntry{key, exec, 0});
+        hit = &c->graphs.back();
+    }
+    hit->last_use = ++c->use_clock;
+    return cudaGraphLaunch(hit->exec, s) == cudaSuccess ? LOGAN_OK : LOGAN_ECUDA;
+}
+
+int set_table(logan_ctx_t* c, const int8_t* levels, int n) {
+    if (!c || !levels || n != kXClasses) return LOGAN_EINVAL;
+    for (int i = 0; i < n; ++i)
+        if (levels[i] < 0 || levels[i] >= kNumLevels) return LOGAN_EINVAL;
+    for (int i = 0; i < n; ++i) c->table.lv[i] = levels[i];
+    return LOGAN_OK;
+}
+
+int load_table_json(logan_ctx_t* c, const char* path) {
+    FILE* f = std::fopen(path, "rb");
+    if (!f) return LOGAN_EINVAL;
+    std::string text;
+    char buf[4096];
+    size_t got;
+    while ((got = std::fread(buf, 1, sizeof buf, f)) > 0) text.append(buf, got);
+    std::fclose(f);
+    const size_t at = text.find("\"levels\"");
+    if (at == std::string::npos) return LOGAN_EINVAL;
+    size_t p = text.find('[', at);
+    if (p == std::string::npos) return LOGAN_EINVAL;
+    int8_t lv[kXClasses];
+    for (int i = 0; i < kXClasses; ++i) {
+        char* end = nullptr;
+        const long v = std::strtol(text.c_str() + p + 1, &end, 10);
+        if (!end || end == text.c_str() + p + 1) return LOGAN_EINVAL;
+        lv[i] = int8_t(v);
+        p = size_t(end - text.c_str());
+        if (i + 1 < kXClasses) {
+            p = text.find(',', p);
+            if (p == std::string::npos) return LOGAN_EINVAL;
+        }
+    }
+    return set_table(c, lv, kXClasses);
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* logan_version(void) { return "logan-gb300 0.1 (sm_103a)"; }
+
+const char* logan_strerror(int code) {
+    switch (code) {
+        case LOGAN_OK: return "ok";
+        case LOGAN_EINVAL: return "invalid argument or invalid pair input";
+        case LOGAN_ENOMEM: return "workspace too small or host allocation failed";
+        case LOGAN_EAGAIN: return "request exceeds the free serving budget";
+        case LOGAN_ECUDA: return "CUDA runtime call failed";
+        case LOGAN_ETIMEOUT: return "bounded wait expired";
+        case LOGAN_ECANCELED: return "request cancelled";
+        case LOGAN_ERANGE: return "band wider than the fallback window";
+        case LOGAN_ENOTFOUND: return "unknown ticket";
+        default: return "unknown error";
+    }
+}
+
+int logan_ctx_create(logan_ctx_t** out, int device, const char* autotune_json) {
+    if (!out) return LOGAN_EINVAL;
+    *out = nullptr;
+    int n_dev = 0;
+    if (cudaGetDeviceCount(&n_dev) != cudaSuccess || device < 0 || device >= n_dev)
+        return LOGAN_ECUDA;
+    logan_ctx* c = new (std::nothrow) logan_ctx();
+    if (!c) return LOGAN_ENOMEM;
+    c->device = device;
+    DeviceGuard g(device);
+    if (cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess) {
+        delete c;
+        return LOGAN_ECUDA;
+    }
+    default_table(c->table);
+    for (int l = 0; l < kNumLevels; ++l)
+        c->blocks_per_sm[l] = l < kWarpLevels ? warp_level_blocks_per_sm(l) : cta_level_blocks_per_sm(l);
+    for (auto& set : c->evs)
+        for (auto& ev : set)
+            if (cudaEventCreate(&ev) != cudaSuccess) {
+                logan_ctx_destroy(c);
+                return LOGAN_ECUDA;
+            }
+    if (autotune_json) {
+        int rc = load_table_json(c, autotune_json);
+        if (rc) {
+            logan_ctx_destroy(c);
+            return rc;
+        }
+    }
+    *out = c;
+    return LOGAN_OK;
+}
+
+void logan_ctx_destroy(logan_ctx_t* c) {
+    if (!c) return;
+    DeviceGuard g(c->device);
+    for (auto& ge : c->graphs)
+        if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    for (auto& set : c->evs)
+        for (auto& ev : set)
+            if (ev) cudaEventDestroy(ev);
+    delete c;
+}
+
+int logan_workspace_size(const logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
+                         uint32_t n_pairs, size_t* bytes) {
+    if (!c || !bytes || !pool_ok(A) || !pool_ok(B)) return LOGAN_EINVAL;
+    *bytes = make_layout(c, A, B, n_pairs).total;
+    return LOGAN_OK;
+}
+
+int logan_extend_batch(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
+                       const logan_seed_t* seeds, uint32_t n_pairs, int32_t match, int32_t mismatch,
+                       int32_t gap, int32_t X, const int32_t* Xs, void* ws, size_t ws_bytes,
+                       logan_result_t* out, void* stream) {
+    return extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs, ws, ws_bytes, out,
+                         stream, 0);
+}
+
+int logan_extend_batch_plain(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
+                             const logan_seed_t* seeds, uint32_t n_pairs, int32_t match,
+                             int32_t mismatch, int32_t gap, int32_t X, const int32_t* Xs, void* ws,
+                             size_t ws_bytes, logan_result_t* out, void* stream) {
+    return extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs, ws, ws_bytes, out,
+                         stream, 1);
+}
+
+int logan_set_option(logan_ctx_t* c, int option, int64_t v) {
+    if (!c) return LOGAN_EINVAL;
+    switch (option) {
+        case LOGAN_OPT_GRAPHS: c->opt_graphs = v ? 1 : 0; return LOGAN_OK;
+        case LOGAN_OPT_TIMING: c->opt_timing = v ? 1 : 0; return LOGAN_OK;
+        case LOGAN_OPT_FORCE_LEVEL:
+            if (v < -1 || v >= kNumLevels) return LOGAN_EINVAL;
+            c->force_level = v;
+            return LOGAN_OK;
+        case LOGAN_OPT_MAX_LEVEL:
+            if (v < 0 || v >= kNumLevels) return LOGAN_EINVAL;
+            c->max_level = v;
+            return LOGAN_OK;
+        case LOGAN_OPT_RING_CAP:
+            if (v < 10 || v > 22) return LOGAN_EINVAL;
+            c->ring_log2 = v;
+            return LOGAN_OK;
+        case LOGAN_OPT_PLAIN_LEVEL:
+            if (v < 0 || v >= kNumLevels) return LOGAN_EINVAL;
+            c->plain_level = v;
+            return LOGAN_OK;
+        default: return LOGAN_EINVAL;
+    }
+}
+
+int logan_get_option(const logan_ctx_t* c, int option, int64_t* v) {
+    if (!c || !v) return LOGAN_EINVAL;
+    switch (option) {
+        case LOGAN_OPT_GRAPHS: *v = c->opt_graphs; return LOGAN_OK;
+        case LOGAN_OPT_TIMING: *v = c->opt_timing; return LOGAN_OK;
+        case LOGAN_OPT_FORCE_LEVEL: *v = c->force_level; return LOGAN_OK;
+        case LOGAN_OPT_MAX_LEVEL: *v = c->max_level; return LOGAN_OK;
+        case LOGAN_OPT_RING_CAP: *v = c->ring_log2; return LOGAN_OK;
+        case LOGAN_OPT_PLAIN_LEVEL: *v = c->plain_level; return LOGAN_OK;
+        default: return LOGAN_EINVAL;
+    }
+}
+
+int logan_num_levels(void) { return kNumLevels; }
+
+int logan_level_info(int level, int* window_cells, int* threads_per_unit) {
+    if (level < 0 || level >= kNumLevels) return LOGAN_EINVAL;
+    if (window_cells) *window_cells = level_window(level);
+    if (threads_per_unit) *threads_per_unit = level_threads(level);
+    return LOGAN_OK;
+}
+
+int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
+    if (!c || !st || back < 0 || back >= kEvSets) return LOGAN_EINVAL;
+    if (!c->timing_pending || uint64_t(back) >= c->timed_calls) return LOGAN_EINVAL;
+    static_assert(kNumLevels <= LOGAN_MAX_LEVELS, "stats layout");
+    DeviceGuard g(c->device);
+    const uint64_t call = c->timed_calls - 1 - uint64_t(back);
+    cudaEvent_t* ev = c->evs[call % kEvSets];
+    const auto& ci = c->calls[call % kEvSets];
+    if (cudaEventSynchronize(ev[kNumLevels + 3]) != cudaSuccess) return LOGAN_ECUDA;
+    std::memset(st, 0, sizeof(*st));
+    for (int l = ci.first_level; l <= ci.max_level; ++l) {
+        // level l runs from ev[l] to the next recorded event
+        const int nxt = l + 1 <= ci.max_level ? l + 1 : kNumLevels;
+        if (cudaEventElapsedTime(&st->level_ms[l], ev[l], ev[nxt]) != cudaSuccess)
+            return LOGAN_ECUDA;
+    }
+    if (cudaEventElapsedTime(&st->level_ms[kNumLevels], ev[kNumLevels], ev[kNumLevels + 2]) !=
+        cudaSuccess)
+        return LOGAN_ECUDA;
+    if (cudaEventElapsedTime(&st->total_ms, ev[kNumLevels + 1], ev[kNumLevels + 3]) != cudaSuccess)
+        return LOGAN_ECUDA;
+    if (back == 0) {
+        // the level counters live in the workspace: valid for the last call only
+        Counters h;
+        if (cudaMemcpy(&h, ci.counters, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
+            return LOGAN_ECUDA;
+        for (int l = 0; l <= kNumLevels; ++l) {
+            st->items[l] = h.tail[l];
+            st->cells[l] = h.cells[l];
+        }
+    }
+    st->launches = ci.launches;
+    return LOGAN_OK;
+}
+
+int logan_last_stats(logan_ctx_t* c, logan_stats_t* st) { return logan_call_stats(c, 0, st); }
+
+// ---- level table (autotune results) ----
+
+int logan_set_level_table(logan_ctx_t* c, const int8_t* levels, int n) {
+    return set_table(c, levels, n);
+}
+
+int logan_get_level_table(const logan_ctx_t* c, int8_t* levels, int n) {
+    if (!c || !levels || n != kXClasses) return LOGAN_EINVAL;
+    for (int i = 0; i < n; ++i) levels[i] = c->table.lv[i];
+    return LOGAN_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,76 @@
+// Host-side declarations shared by the library's translation units.
+#pragma once
+#include <cstddef>
+#include <cstdint>
+#include <cuda_runtime.h>
+
+#include "logan_dev.cuh"
+
+namespace logan {
+
+// Everything an extension kernel needs, passed by value to every launch.
+struct KernelArgs {
+    const uint32_t* wa;      // 2-bit words of pool A
+    const uint32_t* wb;      // 2-bit words of pool B
+    const Item* items;
+    ExtRes* ext;
+    uint32_t* queues;        // (kNumLevels + 1) queues of qcap item ids
+    Counters* counters;
+    int32_t* ring;           // fallback ring slots: n_ring_slots * 3 * ring_cap ints
+    uint32_t qcap;           // = number of items
+    uint32_t n_items;
+    uint32_t ring_cap;       // power of two
+    uint32_t n_ring_slots;
+    uint32_t max_level;      // last register level before the ring
+    Scoring sc;
+};
+
+// extension kernels (xdrop_warp.cu / xdrop_cta.cu / xdrop_ring.cu)
+cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid, cudaStream_t s);
+cudaError_t launch_warp_level_plain(int level, const KernelArgs& ka, cudaStream_t s);
+int warp_level_blocks_per_sm(int level);
+cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int plain, cudaStream_t s);
+int cta_level_blocks_per_sm(int level);
+cudaError_t launch_ring(const KernelArgs& ka, int grid, cudaStream_t s);
+
+// pre/post-processing kernels (prep.cu)
+struct PoolDev {
+    const void* bases;
+    const uint64_t* offsets;
+    const uint32_t* lengths;
+    uint32_t count;
+    uint32_t packed2bit;
+    uint64_t pool_bases;
+    const uint32_t* words;   // 2-bit words used by the kernels
+    uint8_t* bad;            // per-sequence invalid flag
+};
+
+cudaError_t launch_pack(const PoolDev& p, uint32_t* words_out, cudaStream_t s);
+cudaError_t launch_validate(const PoolDev& p, cudaStream_t s);
+cudaError_t launch_split(const PoolDev& A, const PoolDev& B, const void* seeds, uint32_t n_pairs,
+                         Scoring sc, int32_t X, const int32_t* Xs, Item* items, PairInfo* info,
+                         ExtRes* ext, cudaStream_t s);
+constexpr int kBuckets = 128;
+// X class -> starting window level (the autotune table), plus the highest
+// register level in use and an optional X-class filter (-1 = all classes).
+struct LevelTable {
+    int8_t lv[8];
+    int max_level;
+    int only_xclass;
+};
+cudaError_t launch_bin(const Item* items, uint32_t n_items, LevelTable table, int force_level, uint32_t* hist, uint32_t* queues, uint32_t qcap,
+                       Counters* counters, cudaStream_t s);
+cudaError_t launch_reset_counters(Counters* c, uint32_t first_level_items, int first_level,
+                                  cudaStream_t s);
+cudaError_t launch_combine(const void* seeds, const PairInfo* info, const ExtRes* ext,
+                           uint32_t n_pairs, void* out, cudaStream_t s);
+
+// X classes used by the autotune table: X <= 15, <= 35, <= 75, <= 150, <= 300,
+// <= 700, <= 2000, larger.
+constexpr int kXClasses = 8;
+__host__ __device__ inline int x_class(int32_t X) {
+    return X <= 15 ? 0 : X <= 35 ? 1 : X <= 75 ? 2 : X <= 150 ? 3 : X <= 300 ? 4
+         : X <= 700 ? 5 : X <= 2000 ? 6 : 7;
+}
+
+}  // namespace logan

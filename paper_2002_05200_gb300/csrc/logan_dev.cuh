@@ -1,0 +1,99 @@
+// Internal device-side definitions shared by the library's kernels.
+//
+// Data layout in HBM (all inside the caller's workspace, 256-byte aligned
+// chunks; see api.cu for the carve-up):
+//   * 2-bit sequence words: base k of a pool in word k/16, bits 2(k%16)..+1,
+//     codes A0 C1 G2 T3.  Caller-packed pools are read in place; ASCII pools
+//     are packed once into the workspace at the same base positions.
+//   * Item[2*n_pairs]: one extension per pair side (2p = left, 2p+1 = right).
+//     An extension reads stream index q of a' and b' at pool position
+//     pos + dir*q, so the left extension reads both sequences backwards
+//     without a reversed copy (the paper reverses one sequence in memory
+//     for coalescing, Sec. IV-B; here the few bases a step needs come from
+//     L1-resident words, so direction is just an index sign).
+//   * ExtRes[2*n_pairs]: best score, its cell and the computed-cell count of
+//     each extension.
+//   * per-level work queues of item ids + counters.
+//   * fallback ring slots for bands wider than every register window.
+#pragma once
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace logan {
+
+// -infinity of the recurrence.  Every live score lies in
+// [-X, max|score| * (m+n)] subset of (-2^29, 2^29) (host and device
+// validation), so NEG + any score parameter stays below any threshold
+// best - X >= -2^29 and no sum involving NEG overflows int32.
+constexpr int32_t NEG = -(1 << 30);
+
+constexpr int32_t kMaxParam = 1000;
+constexpr int32_t kMaxX = 1 << 29;
+constexpr int64_t kScoreRange = int64_t(1) << 29;
+
+// item flags
+constexpr uint32_t ITEM_LEFT = 1u;   // reads both sequences backwards
+constexpr uint32_t ITEM_SKIP = 2u;   // invalid pair or empty extension: not run
+
+struct Item {
+    int64_t a_pos;   // pool position of a'[0]
+    int64_t b_pos;   // pool position of b'[0]
+    uint32_t m, n;   // lengths of a' and b'
+    int32_t X;
+    uint32_t flags;
+};
+static_assert(sizeof(Item) == 32, "Item layout");
+
+struct ExtRes {
+    int32_t best, bi, bj, status;
+    unsigned long long cells;
+};
+static_assert(sizeof(ExtRes) == 24, "ExtRes layout");
+
+struct PairInfo {
+    int32_t seed_score;
+    int32_t status;
+};
+
+struct Scoring {
+    int32_t match, mismatch, gap;
+};
+
+// Window levels: level k runs a unit of kLevelThreads[k] threads holding
+// kLevelCells[k] cells each (window = threads * cells).  Levels 0..kWarpLevels-1
+// are one warp; the rest are multi-warp units.  After the last level comes the
+// global-memory ring fallback (index kNumLevels).
+constexpr int kNumLevels = 7;
+constexpr int kWarpLevels = 5;
+__host__ __device__ constexpr int level_cells(int k) {
+    return k == 0 ? 1 : k == 1 ? 2 : k == 2 ? 4 : k == 3 ? 8 : k == 4 ? 16 : 8;
+}
+__host__ __device__ constexpr int level_threads(int k) {
+    return k < kWarpLevels ? 32 : (k == 5 ? 128 : 512);
+}
+__host__ __device__ constexpr int level_window(int k) { return level_cells(k) * level_threads(k); }
+
+// Work queues: queue k (k <= kNumLevels) holds the items that level k runs,
+// first those binned to it (longest first), then those escalated from k-1.
+struct Counters {
+    unsigned int tail[kNumLevels + 1];
+    unsigned int head[kNumLevels + 1];
+    unsigned int started[kNumLevels + 1];   // items that began at this level (binning)
+    unsigned int pad;
+    unsigned long long cells[kNumLevels + 1];  // cells of extensions completed at each level
+};
+
+// One 2-bit code of a pool (p must lie inside the pool).
+__device__ __forceinline__ uint32_t code_at(const uint32_t* __restrict__ w, int64_t p) {
+    return (__ldg(w + (p >> 4)) >> (uint32_t(p & 15) * 2u)) & 3u;
+}
+
+// Code of stream index q of an extension operand; indices outside [0, len)
+// return 0 without touching memory (such cells are out of range anyway).
+__device__ __forceinline__ uint32_t stream_code(const uint32_t* __restrict__ w, int64_t pos,
+                                                int dir, uint32_t len, int64_t q) {
+    if (q < 0 || q >= int64_t(len)) return 0u;
+    return code_at(w, pos + (dir > 0 ? q : -q));
+}
+
+}  // namespace logan

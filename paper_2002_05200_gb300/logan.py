@@ -1,0 +1,270 @@
+"""Thin Python binding of the C ABI in include/logan.h (ctypes).
+
+Argument marshalling only: every step of the extension runs in the CUDA
+kernels of ``_build/liblogan.so``.  PyTorch supplies device memory and
+streams.  If the library is missing this module raises -- there is no CPU
+fallback.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+from dataclasses import dataclass
+from typing import Optional
+
+import numpy as np
+
+HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(HERE, "_build", "liblogan.so")
+
+OK = 0
+EINVAL, ENOMEM, EAGAIN, ECUDA, ETIMEOUT, ECANCELED, ERANGE, ENOTFOUND = \
+    -22, -12, -11, -5, -110, -125, -34, -2
+OPT_GRAPHS, OPT_TIMING, OPT_FORCE_LEVEL, OPT_MAX_LEVEL, OPT_RING_CAP, OPT_PLAIN_LEVEL = 1, 2, 3, 4, 5, 6
+X_CLASSES = 8
+
+RESULT_DTYPE = np.dtype([("score", "<i4"), ("left", "<i4"), ("right", "<i4"), ("status", "<i4"),
+                         ("begA", "<u4"), ("begB", "<u4"), ("endA", "<u4"), ("endB", "<u4"),
+                         ("cells", "<u8")])
+assert RESULT_DTYPE.itemsize == 40
+
+EXPORTED = ["logan_version", "logan_strerror", "logan_ctx_create", "logan_ctx_destroy",
+            "logan_workspace_size", "logan_extend_batch", "logan_extend_batch_plain",
+            "logan_set_option", "logan_get_option", "logan_num_levels", "logan_level_info",
+            "logan_last_stats", "logan_call_stats", "logan_set_level_table",
+            "logan_get_level_table", "logan_intpeak"]
+
+
+class SeqsT(ctypes.Structure):
+    _fields_ = [("bases", ctypes.c_void_p), ("offsets", ctypes.c_void_p),
+                ("lengths", ctypes.c_void_p), ("count", ctypes.c_uint32),
+                ("packed2bit", ctypes.c_uint32), ("pool_bases", ctypes.c_uint64)]
+
+
+MAX_LEVELS = 8
+
+
+class StatsT(ctypes.Structure):
+    _fields_ = [("level_ms", ctypes.c_float * (MAX_LEVELS + 1)), ("total_ms", ctypes.c_float),
+                ("items", ctypes.c_uint32 * (MAX_LEVELS + 1)),
+                ("cells", ctypes.c_uint64 * (MAX_LEVELS + 1)), ("launches", ctypes.c_uint32)]
+
+
+class LoganError(RuntimeError):
+    def __init__(self, code: int, what: str):
+        super().__init__(f"{what}: {strerror(code)} ({code})")
+        self.code = code
+
+
+_lib = None
+
+
+def lib():
+    """The loaded library (raises if it has not been built)."""
+    global _lib
+    if _lib is None:
+        if not os.path.exists(LIB_PATH):
+            raise RuntimeError(f"CUDA library not built: {LIB_PATH} is missing "
+                               "(run paper_2002_05200_gb300.build.build())")
+        L = ctypes.CDLL(LIB_PATH)
+        p, i32, u32, i64 = ctypes.c_void_p, ctypes.c_int32, ctypes.c_uint32, ctypes.c_int64
+        L.logan_version.restype = ctypes.c_char_p
+        L.logan_strerror.restype = ctypes.c_char_p
+        L.logan_strerror.argtypes = [ctypes.c_int]
+        L.logan_ctx_create.argtypes = [ctypes.POINTER(p), ctypes.c_int, ctypes.c_char_p]
+        L.logan_ctx_destroy.argtypes = [p]
+        L.logan_ctx_destroy.restype = None
+        L.logan_workspace_size.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT), u32,
+                                           ctypes.POINTER(ctypes.c_size_t)]
+        ext_args = [p, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT), p, u32, i32, i32, i32, i32, p,
+                    p, ctypes.c_size_t, p, p]
+        L.logan_extend_batch.argtypes = ext_args
+        L.logan_extend_batch_plain.argtypes = ext_args
+        L.logan_set_option.argtypes = [p, ctypes.c_int, i64]
+        L.logan_get_option.argtypes = [p, ctypes.c_int, ctypes.POINTER(i64)]
+        L.logan_level_info.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                       ctypes.POINTER(ctypes.c_int)]
+        L.logan_last_stats.argtypes = [p, ctypes.POINTER(StatsT)]
+        L.logan_call_stats.argtypes = [p, ctypes.c_int, ctypes.POINTER(StatsT)]
+        L.logan_intpeak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
+                                    ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
+        L.logan_set_level_table.argtypes = [p, ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
+        L.logan_get_level_table.argtypes = [p, ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
+        _lib = L
+    return _lib
+
+
+def strerror(code: int) -> str:
+    return lib().logan_strerror(code).decode()
+
+
+def version() -> str:
+    return lib().logan_version().decode()
+
+
+def num_levels() -> int:
+    return int(lib().logan_num_levels())
+
+
+def level_info(level: int):
+    w, t = ctypes.c_int(), ctypes.c_int()
+    _check(lib().logan_level_info(level, ctypes.byref(w), ctypes.byref(t)), "level_info")
+    return w.value, t.value
+
+
+def intpeak(device: int = 0, op: int = 0, iters: int = 4000):
+    """(thread-instructions per second, ms) of the integer microbenchmark."""
+    r, ms = ctypes.c_double(), ctypes.c_float()
+    _check(lib().logan_intpeak(device, op, iters, ctypes.byref(r), ctypes.byref(ms)),
+           "logan_intpeak")
+    return r.value, ms.value
+
+
+def _check(rc: int, what: str):
+    if rc != OK:
+        raise LoganError(rc, what)
+
+
+@dataclass
+class DevicePool:
+    """Sequences resident on the device (torch tensors) + their C view."""
+    bases: "torch.Tensor"       # uint8 ASCII, or int32 words holding 2-bit codes
+    offsets: "torch.Tensor"     # int64 (read as uint64)
+    lengths: "torch.Tensor"     # int32 (read as uint32)
+    packed2bit: bool
+    pool_bases: int
+
+    @property
+    def count(self) -> int:
+        return int(self.lengths.numel())
+
+    def c(self) -> SeqsT:
+        return SeqsT(self.bases.data_ptr() if self.bases.numel() else None,
+                     self.offsets.data_ptr() if self.count else None,
+                     self.lengths.data_ptr() if self.count else None,
+                     self.count, 1 if self.packed2bit else 0, self.pool_bases)
+
+
+def pool_to_device(bases: np.ndarray, offsets: np.ndarray, lengths: np.ndarray,
+                   packed2bit: bool, pool_bases: int, device="cuda") -> DevicePool:
+    import torch
+    if packed2bit:
+        b = torch.from_numpy(np.ascontiguousarray(bases).view(np.int32)).to(device)
+    else:
+        b = torch.from_numpy(np.ascontiguousarray(bases, dtype=np.uint8)).to(device)
+    o = torch.from_numpy(np.ascontiguousarray(offsets, dtype=np.uint64).view(np.int64)).to(device)
+    n = torch.from_numpy(np.ascontiguousarray(lengths, dtype=np.uint32).view(np.int32)).to(device)
+    return DevicePool(b, o, n, packed2bit, int(pool_bases))
+
+
+def seeds_to_device(seeds: np.ndarray, device="cuda"):
+    import torch
+    arr = np.stack([seeds[f] for f in ("idxA", "idxB", "posA", "posB", "len")], axis=1)
+    return torch.from_numpy(np.ascontiguousarray(arr.astype(np.uint32)).view(np.int32)).to(device)
+
+
+def results_to_numpy(out) -> np.ndarray:
+    """Device result tensor (int32 [n, 10]) -> structured array of RESULT_DTYPE."""
+    return out.cpu().numpy().view(RESULT_DTYPE).reshape(-1)
+
+
+class Context:
+    """A library context on one GPU (logan_ctx_t)."""
+
+    def __init__(self, device: int = 0, autotune_json: Optional[str] = None):
+        self._h = ctypes.c_void_p()
+        _check(lib().logan_ctx_create(ctypes.byref(self._h), device,
+                                      autotune_json.encode() if autotune_json else None),
+               "logan_ctx_create")
+        self.device = device
+
+    def close(self):
+        if self._h:
+            lib().logan_ctx_destroy(self._h)
+            self._h = ctypes.c_void_p()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def set_option(self, opt: int, value: int):
+        _check(lib().logan_set_option(self._h, opt, int(value)), "logan_set_option")
+
+    def get_option(self, opt: int) -> int:
+        v = ctypes.c_int64()
+        _check(lib().logan_get_option(self._h, opt, ctypes.byref(v)), "logan_get_option")
+        return v.value
+
+    def set_level_table(self, levels):
+        arr = (ctypes.c_int8 * X_CLASSES)(*[int(v) for v in levels])
+        _check(lib().logan_set_level_table(self._h, arr, X_CLASSES), "logan_set_level_table")
+
+    def level_table(self):
+        arr = (ctypes.c_int8 * X_CLASSES)()
+        _check(lib().logan_get_level_table(self._h, arr, X_CLASSES), "logan_get_level_table")
+        return list(arr)
+
+    def workspace_size(self, A: DevicePool, B: DevicePool, n_pairs: int) -> int:
+        n = ctypes.c_size_t()
+        ca, cb = A.c(), B.c()
+        _check(lib().logan_workspace_size(self._h, ctypes.byref(ca), ctypes.byref(cb), n_pairs,
+                                          ctypes.byref(n)), "logan_workspace_size")
+        return n.value
+
+    def workspace(self, A: DevicePool, B: DevicePool, n_pairs: int):
+        import torch
+        return torch.empty(max(1, self.workspace_size(A, B, n_pairs)), dtype=torch.uint8,
+                           device=f"cuda:{self.device}")
+
+    def extend(self, A: DevicePool, B: DevicePool, seeds, match: int = 1, mismatch: int = -1,
+               gap: int = -1, X: int = 50, X_per_pair=None, workspace=None, out=None,
+               stream=None, plain: bool = False):
+        """Runs logan_extend_batch(_plain); returns the int32 [n, 10] result tensor
+        (asynchronous on `stream`, default torch's current stream)."""
+        import torch
+        n = int(seeds.shape[0])
+        if out is None:
+            out = torch.empty((max(n, 1), 10), dtype=torch.int32, device=f"cuda:{self.device}")
+        if workspace is None:
+            workspace = self.workspace(A, B, n)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        ca, cb = A.c(), B.c()
+        fn = lib().logan_extend_batch_plain if plain else lib().logan_extend_batch
+        rc = fn(self._h, ctypes.byref(ca), ctypes.byref(cb),
+                seeds.data_ptr() if n else None, n, match, mismatch, gap, X,
+                X_per_pair.data_ptr() if X_per_pair is not None else None,
+                workspace.data_ptr(), workspace.numel(), out.data_ptr(),
+                ctypes.c_void_p(stream.cuda_stream))
+        _check(rc, "logan_extend_batch_plain" if plain else "logan_extend_batch")
+        return out[:n]
+
+    def last_stats(self, back: int = 0) -> dict:
+        """Per-level device ms / items / completed cells of a call made with
+        OPT_TIMING (back = 0: the last one; index num_levels() = global-memory
+        fallback)."""
+        st = StatsT()
+        _check(lib().logan_call_stats(self._h, back, ctypes.byref(st)), "logan_call_stats")
+        n = num_levels() + 1
+        return dict(level_ms=list(st.level_ms)[:n], total_ms=st.total_ms,
+                    items=list(st.items)[:n], cells=list(st.cells)[:n], launches=st.launches)
+
+
+def batch_to_device(b, packed2bit: Optional[bool] = None, device="cuda"):
+    """synth.Batch -> (DevicePool A, DevicePool B, seeds tensor, X_per_pair tensor or None)."""
+    import torch
+    from . import synth
+    packed = bool(b.meta.get("packed2bit", False)) if packed2bit is None else packed2bit
+
+    def pool(p, off, ln):
+        if packed:
+            return pool_to_device(synth.pack2bit(p), off, ln, True, p.size, device)
+        return pool_to_device(p, off, ln, False, p.size, device)
+
+    A = pool(b.poolA, b.offA, b.lenA)
+    B = A if b.shared_pool else pool(b.poolB, b.offB, b.lenB)
+    S = seeds_to_device(b.seeds, device)
+    Xs = None if b.Xs is None else torch.from_numpy(np.ascontiguousarray(b.Xs, np.int32)).to(device)
+    return A, B, S, Xs

@@ -1,0 +1,181 @@
+"""GPU path vs the CPU oracle, bit-exact on every integer field (score,
+left/right best, four coordinates, computed cells, status)."""
+import numpy as np
+import pytest
+
+from paper_2002_05200_gb300 import logan, synth
+from tests.gpu_common import assert_same, run_gpu, run_oracle
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = logan.Context(0)
+    yield c
+    c.close()
+
+
+@pytest.fixture(autouse=True)
+def _reset(ctx):
+    for opt, v in ((logan.OPT_FORCE_LEVEL, -1), (logan.OPT_MAX_LEVEL, logan.num_levels() - 1),
+                   (logan.OPT_GRAPHS, 0), (logan.OPT_RING_CAP, 16), (logan.OPT_PLAIN_LEVEL, 1),
+                   (logan.OPT_TIMING, 0)):
+        ctx.set_option(opt, v)
+    yield
+
+
+def test_uniform_pairs_ascii(ctx):
+    b = synth.uniform_pairs()
+    ref = run_oracle(b)
+    assert_same(run_gpu(ctx, b), ref, "persistent")
+    assert_same(run_gpu(ctx, b, plain=True), ref, "plain")
+
+
+def test_lognormal_packed(ctx):
+    b = synth.lognormal_batch(n_pairs=300)
+    ref = run_oracle(b)
+    assert_same(run_gpu(ctx, b, packed2bit=True), ref, "persistent")
+    assert_same(run_gpu(ctx, b, packed2bit=True, plain=True), ref, "plain")
+
+
+def test_uneven_per_pair_x(ctx):
+    b = synth.uneven_batch(n_pairs=200, max_len=40_000)
+    ref = run_oracle(b)
+    assert_same(run_gpu(ctx, b, packed2bit=True), ref, "persistent")
+    assert_same(run_gpu(ctx, b, plain=True), ref, "plain")
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tiny_edge_cases(ctx, seed):
+    # lengths 0..40, seeds of 0..17 bases anywhere (incl. at both ends),
+    # X in {0,1,2,5,10,50}: empty sides, X below the gap cost, one-cell bands
+    b = synth.tiny_pairs(3000, 40, seed=seed)
+    ref = run_oracle(b)
+    assert_same(run_gpu(ctx, b), ref, "persistent")
+    assert_same(run_gpu(ctx, b, packed2bit=True, plain=True), ref, "plain")
+
+
+@pytest.mark.parametrize("level", range(7))
+def test_every_window_level(ctx, level):
+    # each level started directly; narrower bands stay, wider ones escalate
+    b = synth.uneven_batch(n_pairs=120, max_len=12_000, seed=21)
+    ref = run_oracle(b)
+    ctx.set_option(logan.OPT_FORCE_LEVEL, level)
+    assert_same(run_gpu(ctx, b, packed2bit=True), ref, f"level {level}")
+    ctx.set_option(logan.OPT_PLAIN_LEVEL, level)
+    assert_same(run_gpu(ctx, b, plain=True), ref, f"plain level {level}")
+
+
+def test_ring_fallback_only(ctx):
+    # max level 0 sends every band wider than 31 cells to the ring kernel
+    b = synth.uniform_pairs(n_pairs=60, X=50)
+    ref = run_oracle(b)
+    ctx.set_option(logan.OPT_MAX_LEVEL, 0)
+    ctx.set_option(logan.OPT_FORCE_LEVEL, 0)
+    assert_same(run_gpu(ctx, b), ref, "ring")
+
+
+def test_unpruned_wide_bands(ctx):
+    # X beyond any possible drop: the band is the whole matrix, wider than
+    # every register window for the longer pairs
+    rng = np.random.default_rng(3)
+    b = synth.tiny_pairs(40, 600, seed=4, X_choices=(200_000,))
+    ref = run_oracle(b)
+    assert_same(run_gpu(ctx, b), ref, "unpruned")
+
+
+def test_ring_too_narrow_reports_erange(ctx):
+    b = synth.tiny_pairs(30, 3000, seed=8, X_choices=(1_000_000,))
+    ctx.set_option(logan.OPT_RING_CAP, 10)
+    ctx.set_option(logan.OPT_MAX_LEVEL, 0)
+    ctx.set_option(logan.OPT_FORCE_LEVEL, 0)
+    g = run_gpu(ctx, b)
+    ref = run_oracle(b)
+    # nothing is pruned, so an extension's widest anti-diagonal holds
+    # min(m, n) + 1 cells; wider than the 1024-cell ring -> LOGAN_ERANGE
+    s = b.seeds
+    lA, lB = b.lenA[s["idxA"]].astype(np.int64), b.lenB[s["idxB"]].astype(np.int64)
+    left = np.minimum(s["posA"], s["posB"]).astype(np.int64) + 1
+    right = np.minimum(lA - s["posA"] - s["len"], lB - s["posB"] - s["len"]) + 1
+    wide = np.maximum(left, right) > 1024
+    assert wide.any() and (~wide).any()
+    assert np.all(g["status"][wide] == logan.ERANGE)
+    for f in ("score", "cells", "begA", "endB"):
+        assert np.all(g[f][wide] == 0)
+        assert np.array_equal(g[f][~wide].astype(np.int64), ref[f][~wide].astype(np.int64))
+
+
+@pytest.mark.parametrize("scheme", [(2, -3, -2), (5, -4, -7), (1, -1, 0), (3, 1, -2), (1000, -1000, -1000)])
+def test_scoring_schemes(ctx, scheme):
+    b = synth.uniform_pairs(n_pairs=150, length=600, X=40, seed=5)
+    b.match, b.mismatch, b.gap = scheme
+    ref = run_oracle(b)
+    assert_same(run_gpu(ctx, b), ref, str(scheme))
+
+
+def test_invalid_pairs(ctx):
+    b = synth.tiny_pairs(200, 30, seed=12)
+    poolA = b.poolA.copy()
+    # a non-ACGT base in some sequences, seeds past the end in others
+    poolA[::97] = ord("N")
+    b.poolA = poolA
+    seeds = b.seeds.copy()
+    seeds["posA"][::13] = b.lenA[seeds["idxA"][::13]] + 1
+    seeds["idxB"][5] = 10_000
+    b.seeds = seeds
+    Xs = b.Xs.copy()
+    Xs[7] = -1
+    b.Xs = Xs
+    ref = run_oracle(b)
+    g = run_gpu(ctx, b)
+    assert np.all(g["status"][ref["status"] != 0] == logan.EINVAL)
+    assert_same(g, ref, "invalid")
+
+
+def test_graph_replay_matches(ctx):
+    b = synth.uniform_pairs(n_pairs=300)
+    ref = run_oracle(b)
+    import torch
+    A, B, S, Xs = logan.batch_to_device(b)
+    ctx.set_option(logan.OPT_GRAPHS, 1)
+    stream = torch.cuda.Stream()
+    ws = ctx.workspace(A, B, b.n_pairs)
+    out = torch.empty((b.n_pairs, 10), dtype=torch.int32, device="cuda")
+    with torch.cuda.stream(stream):
+        for _ in range(3):
+            out.zero_()
+            ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, workspace=ws, out=out,
+                       stream=stream)
+    stream.synchronize()
+    assert_same(logan.results_to_numpy(out), ref, "graph")
+
+
+def test_argument_errors(ctx):
+    import torch
+    b = synth.uniform_pairs(n_pairs=4)
+    A, B, S, _ = logan.batch_to_device(b)
+    for args in ((1, -1, 1, 5), (1, 2, -1, 5), (1, -1, -1, -1), (1001, -1, -1, 5),
+                 (1, -1, -1, (1 << 29) + 1)):
+        with pytest.raises(logan.LoganError) as e:
+            ctx.extend(A, B, S, *args)
+        assert e.value.code == logan.EINVAL
+    ws = torch.empty(16, dtype=torch.uint8, device="cuda")
+    with pytest.raises(logan.LoganError) as e:
+        ctx.extend(A, B, S, workspace=ws)
+    assert e.value.code == logan.ENOMEM
+
+
+def test_timing_and_level_counts(ctx):
+    b = synth.lognormal_batch(n_pairs=200)
+    ctx.set_option(logan.OPT_TIMING, 1)
+    g = run_gpu(ctx, b, packed2bit=True)
+    st = ctx.last_stats()
+    assert st["total_ms"] > 0 and all(v >= 0 for v in st["level_ms"])
+    assert sum(st["items"]) >= np.count_nonzero(b.lenA > 0)
+    # every completed extension's cells are attributed to exactly one level
+    assert sum(st["cells"]) == int(g["cells"].sum())
+    assert st["launches"] >= 10
