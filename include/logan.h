@@ -160,6 +160,39 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                              void *workspace, size_t ws_bytes,
                              logan_result_t *out, void *stream);
 
+/*
+ * Same operation and results as logan_extend_batch, for callers that cannot
+ * allocate device memory -- e.g. a host whose GPU memory is owned by another
+ * allocator, or a latency-critical loop that must not call cudaMalloc /
+ * cudaFree (both can synchronise the device and stall unrelated streams).
+ * The paper has no counterpart: this is a deployment variant of the batch
+ * call.  The caller still provides inputs and `out`; the pipeline's scratch
+ * memory is one static device array of LOGAN_NOALLOC_SCRATCH_BYTES that
+ * every GPU loading the library holds until the process exits.
+ *   - No cudaMalloc/cudaFree or other allocating call, and no CUDA graph is
+ *     built (the context's graph option is ignored for this call).
+ *   - The fallback window for very wide bands is LOGAN_NOALLOC_RING_ROWS
+ *     rows (wider bands give LOGAN_ERANGE for that pair).
+ *   - A batch whose scratch need (logan_workspace_size with that window)
+ *     exceeds LOGAN_NOALLOC_SCRATCH_BYTES is rejected with LOGAN_ENOMEM
+ *     before anything is launched (about 140K pairs of 2-bit input fit).
+ *   - The first call on a device looks up the array's device address (with
+ *     that device current); make that first call before any stream capture.
+ *   - All no-alloc calls on a device share the array, which keeps the last
+ *     call's contents; the pipeline initialises everything it reads, so no
+ *     clearing is needed between calls, but calls that overlap on the GPU
+ *     (different streams, or different contexts on the same device) race on
+ *     it: order them on one stream or synchronise between them.
+ */
+#define LOGAN_NOALLOC_SCRATCH_BYTES (32u << 20)
+#define LOGAN_NOALLOC_RING_LOG2 12
+#define LOGAN_NOALLOC_RING_ROWS (1 << LOGAN_NOALLOC_RING_LOG2)
+int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
+                               const logan_seqs_t *seqsB, const logan_seed_t *seeds,
+                               uint32_t n_pairs, int32_t match, int32_t mismatch, int32_t gap,
+                               int32_t X, const int32_t *X_per_pair,
+                               logan_result_t *out, void *stream);
+
 /* Options (logan_set_option / logan_get_option):
  *   LOGAN_OPT_GRAPHS        1: capture + replay CUDA graphs (default 0)
  *   LOGAN_OPT_TIMING        1: record CUDA events around the extension
@@ -178,6 +211,7 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
 #define LOGAN_OPT_MAX_LEVEL 4
 #define LOGAN_OPT_RING_CAP 5
 #define LOGAN_OPT_PLAIN_LEVEL 6
+#define LOGAN_OPT_DEVICE 7       /* read-only: the context's CUDA device */
 int logan_set_option(logan_ctx_t *ctx, int option, int64_t value);
 int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
 

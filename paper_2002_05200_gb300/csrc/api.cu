@@ -478,6 +478,7 @@ int logan_get_option(const logan_ctx_t* c, int option, int64_t* v) {
         case LOGAN_OPT_MAX_LEVEL: *v = c->max_level; return LOGAN_OK;
         case LOGAN_OPT_RING_CAP: *v = c->ring_log2; return LOGAN_OK;
         case LOGAN_OPT_PLAIN_LEVEL: *v = c->plain_level; return LOGAN_OK;
+        case LOGAN_OPT_DEVICE: *v = c->device; return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }
