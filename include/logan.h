@@ -260,6 +260,88 @@ int logan_intpeak(int device, int op, int iters, double *instr_per_s, float *ms)
 int logan_set_level_table(logan_ctx_t *ctx, const int8_t *levels, int n);
 int logan_get_level_table(const logan_ctx_t *ctx, int8_t *levels, int n);
 
+/* Autotuner (the paper schedules threads in proportion to X, Sec. IV-B; here
+ * the unit per X class is measured): for every X class present in the
+ * sample batch, runs the batch restricted to that class once per start
+ * level (reps times, keeping the fastest), times the extension kernels with
+ * CUDA events and stores the fastest level in the context's table.
+ * Arguments as logan_extend_batch; synchronous (it waits for every run and
+ * copies X_per_pair to the host).  ms_table (nullable, host float
+ * [LOGAN_X_CLASSES * logan_num_levels()]) receives the measured ms, -1 for
+ * classes absent from the sample.  The context's other options are
+ * restored afterwards. */
+int logan_autotune(logan_ctx_t *ctx, const logan_seqs_t *seqsA, const logan_seqs_t *seqsB,
+                   const logan_seed_t *seeds, uint32_t n_pairs, int32_t match, int32_t mismatch,
+                   int32_t gap, int32_t X, const int32_t *X_per_pair, void *workspace,
+                   size_t ws_bytes, logan_result_t *out, void *stream, int reps,
+                   float *ms_table);
+/* Writes the table as JSON ({"gpu": ..., "sms": ..., "levels": [...]}),
+ * readable by logan_ctx_create. */
+int logan_autotune_save(const logan_ctx_t *ctx, const char *path);
+
+/* ---------------------------------------------------------------------------
+ * Serving loop (continuous batching).
+ *
+ * A server owns one device arena of budget_bytes (one cudaMalloc at
+ * creation) and max_inflight CUDA streams ("slots").  Requests are host
+ * batches; a scheduler thread admits them in arrival order as soon as a slot
+ * is idle and the arena has room for the request's device copy (pools,
+ * seeds, results and workspace), enqueues copy-in, the extension pipeline and
+ * copy-out on the slot's stream and returns the bytes when the stream
+ * reaches the request's end.  Requests on different slots overlap on the GPU;
+ * each has its own workspace, so its results are the same alone and in any
+ * mix.  The server uses the context exclusively (graphs and timing off)
+ * until logan_server_destroy; do not call other functions on that context
+ * meanwhile.
+ */
+typedef struct logan_server logan_server_t;
+
+/* One request.  Every pointer is HOST memory owned by the caller and must
+ * stay valid until the request is done (pinned memory lets the copies
+ * overlap with the GPU; pageable memory works but blocks the scheduler
+ * thread during its copies).  A.bases/B.bases: ASCII bytes (pool_bases of
+ * them) or 2-bit words (ceil(pool_bases/16) of them).  same_pool != 0: B is
+ * A.  results: n_pairs logan_result_t written by the server. */
+typedef struct {
+    logan_seqs_t A, B;
+    int32_t same_pool;
+    const logan_seed_t *seeds;
+    uint32_t n_pairs;
+    int32_t match, mismatch, gap, X;
+    const int32_t *X_per_pair;
+    logan_result_t *results;
+} logan_request_t;
+
+typedef struct {
+    uint32_t queued, running;
+    uint64_t completed, failed, cancelled;
+    uint64_t budget_bytes, used_bytes, peak_bytes;
+} logan_server_stats_t;
+
+/* max_inflight in [1, 64]; max_queued: submissions beyond this many waiting
+ * requests get LOGAN_EAGAIN (0 = 2^20). */
+int logan_server_create(logan_ctx_t *ctx, size_t budget_bytes, int max_inflight,
+                        uint32_t max_queued, logan_server_t **server);
+/* Queues a request; returns its ticket.  LOGAN_ENOMEM: the request alone
+ * needs more than the whole budget; LOGAN_EAGAIN: the queue is full (retry
+ * later); LOGAN_EINVAL: bad arguments. */
+int logan_server_submit(logan_server_t *server, const logan_request_t *req, uint64_t *ticket);
+/* Non-blocking: *done = 1 once the request finished (then *status is its
+ * status -- LOGAN_OK, LOGAN_ECANCELED or the launch error -- and *latency_ms
+ * the submit-to-results-on-host time; the ticket is retired). */
+int logan_server_poll(logan_server_t *server, uint64_t ticket, int *done, int *status,
+                      double *latency_ms);
+/* Blocking, bounded: returns LOGAN_ETIMEOUT if the request is not done
+ * within timeout_ms (< 0 waits forever); otherwise like poll with done = 1. */
+int logan_server_wait(logan_server_t *server, uint64_t ticket, int timeout_ms, int *status,
+                      double *latency_ms);
+/* Cancels a request that has not been admitted yet (LOGAN_EAGAIN once it
+ * runs: an admitted request always completes). */
+int logan_server_cancel(logan_server_t *server, uint64_t ticket);
+int logan_server_stats(logan_server_t *server, logan_server_stats_t *stats);
+/* Cancels queued requests, waits for running ones, frees the arena. */
+int logan_server_destroy(logan_server_t *server);
+
 #ifdef __cplusplus
 }
 #endif

@@ -529,6 +529,85 @@ int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
 
 int logan_last_stats(logan_ctx_t* c, logan_stats_t* st) { return logan_call_stats(c, 0, st); }
 
+// ---- autotuner: X class -> fastest start level ----
+
+int logan_autotune(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
+                   const logan_seed_t* seeds, uint32_t n_pairs, int32_t match, int32_t mismatch,
+                   int32_t gap, int32_t X, const int32_t* Xs, void* ws, size_t ws_bytes,
+                   logan_result_t* out, void* stream, int reps, float* ms_table) {
+    if (!c || reps < 1 || n_pairs == 0) return LOGAN_EINVAL;
+    DeviceGuard g(c->device);
+    // which X classes does the sample hold?
+    bool present[kXClasses] = {};
+    if (Xs) {
+        std::vector<int32_t> hx(n_pairs);
+        if (cudaMemcpy(hx.data(), Xs, sizeof(int32_t) * n_pairs, cudaMemcpyDeviceToHost) !=
+            cudaSuccess)
+            return LOGAN_ECUDA;
+        for (int32_t v : hx)
+            if (v >= 0 && v <= kMaxX) present[x_class(v)] = true;
+    } else {
+        present[x_class(X)] = true;
+    }
+    const int64_t save_force = c->force_level, save_timing = c->opt_timing,
+                  save_graphs = c->opt_graphs;
+    const LevelTable save_table = c->table;
+    const int maxl = int(c->max_level);
+    c->opt_timing = 1;
+    c->opt_graphs = 0;
+    int rc = LOGAN_OK;
+    int8_t chosen[kXClasses];
+    for (int k = 0; k < kXClasses; ++k) chosen[k] = save_table.lv[k];
+    if (ms_table)
+        for (int k = 0; k < kXClasses * kNumLevels; ++k) ms_table[k] = -1.f;
+    for (int cls = 0; cls < kXClasses && rc == LOGAN_OK; ++cls) {
+        if (!present[cls]) continue;
+        c->table.only_xclass = cls;
+        float best_ms = 0.f;
+        int best_level = -1;
+        for (int lvl = 0; lvl <= maxl && rc == LOGAN_OK; ++lvl) {
+            c->force_level = lvl;
+            float t_min = -1.f;
+            for (int r = 0; r < reps && rc == LOGAN_OK; ++r) {
+                rc = extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs, ws,
+                                   ws_bytes, out, stream, 0);
+                logan_stats_t st;
+                if (rc == LOGAN_OK) rc = logan_call_stats(c, 0, &st);
+                if (rc != LOGAN_OK) break;
+                float t = st.level_ms[kNumLevels];
+                for (int l = 0; l <= maxl; ++l) t += st.level_ms[l];
+                if (t_min < 0.f || t < t_min) t_min = t;
+            }
+            if (rc != LOGAN_OK) break;
+            if (ms_table) ms_table[cls * kNumLevels + lvl] = t_min;
+            if (best_level < 0 || t_min < best_ms) {
+                best_ms = t_min;
+                best_level = lvl;
+            }
+        }
+        if (best_level >= 0) chosen[cls] = int8_t(best_level);
+    }
+    c->force_level = save_force;
+    c->opt_timing = save_timing;
+    c->opt_graphs = save_graphs;
+    c->table = save_table;
+    if (rc == LOGAN_OK) rc = set_table(c, chosen, kXClasses);
+    return rc;
+}
+
+int logan_autotune_save(const logan_ctx_t* c, const char* path) {
+    if (!c || !path) return LOGAN_EINVAL;
+    cudaDeviceProp prop;
+    if (cudaGetDeviceProperties(&prop, c->device) != cudaSuccess) return LOGAN_ECUDA;
+    FILE* f = std::fopen(path, "wb");
+    if (!f) return LOGAN_EINVAL;
+    std::fprintf(f, "{\"gpu\": \"%s\", \"sms\": %d, \"x_class_upper\": [15, 35, 75, 150, 300, 700, 2000, 536870912], \"levels\": [",
+                 prop.name, prop.multiProcessorCount);
+    for (int i = 0; i < kXClasses; ++i) std::fprintf(f, "%s%d", i ? ", " : "", int(c->table.lv[i]));
+    std::fprintf(f, "]}\n");
+    return std::fclose(f) == 0 ? LOGAN_OK : LOGAN_EINVAL;
+}
+
 // ---- level table (autotune results) ----
 
 int logan_set_level_table(logan_ctx_t* c, const int8_t* levels, int n) {

@@ -32,7 +32,10 @@ EXPORTED = ["logan_version", "logan_strerror", "logan_ctx_create", "logan_ctx_de
             "logan_workspace_size", "logan_extend_batch", "logan_extend_batch_plain",
             "logan_set_option", "logan_get_option", "logan_num_levels", "logan_level_info",
             "logan_last_stats", "logan_call_stats", "logan_set_level_table",
-            "logan_get_level_table", "logan_intpeak"]
+            "logan_get_level_table", "logan_intpeak", "logan_autotune", "logan_autotune_save",
+            "logan_extend_batch_noalloc", "logan_server_create", "logan_server_submit",
+            "logan_server_poll", "logan_server_wait", "logan_server_cancel", "logan_server_stats",
+            "logan_server_destroy"]
 
 
 class SeqsT(ctypes.Structure):
@@ -48,6 +51,21 @@ class StatsT(ctypes.Structure):
     _fields_ = [("level_ms", ctypes.c_float * (MAX_LEVELS + 1)), ("total_ms", ctypes.c_float),
                 ("items", ctypes.c_uint32 * (MAX_LEVELS + 1)),
                 ("cells", ctypes.c_uint64 * (MAX_LEVELS + 1)), ("launches", ctypes.c_uint32)]
+
+
+class RequestT(ctypes.Structure):
+    _fields_ = [("A", SeqsT), ("B", SeqsT), ("same_pool", ctypes.c_int32),
+                ("seeds", ctypes.c_void_p), ("n_pairs", ctypes.c_uint32),
+                ("match", ctypes.c_int32), ("mismatch", ctypes.c_int32), ("gap", ctypes.c_int32),
+                ("X", ctypes.c_int32), ("X_per_pair", ctypes.c_void_p),
+                ("results", ctypes.c_void_p)]
+
+
+class ServerStatsT(ctypes.Structure):
+    _fields_ = [("queued", ctypes.c_uint32), ("running", ctypes.c_uint32),
+                ("completed", ctypes.c_uint64), ("failed", ctypes.c_uint64),
+                ("cancelled", ctypes.c_uint64), ("budget_bytes", ctypes.c_uint64),
+                ("used_bytes", ctypes.c_uint64), ("peak_bytes", ctypes.c_uint64)]
 
 
 class LoganError(RuntimeError):
@@ -86,6 +104,19 @@ def lib():
                                        ctypes.POINTER(ctypes.c_int)]
         L.logan_last_stats.argtypes = [p, ctypes.POINTER(StatsT)]
         L.logan_call_stats.argtypes = [p, ctypes.c_int, ctypes.POINTER(StatsT)]
+        L.logan_autotune.argtypes = ext_args + [ctypes.c_int, ctypes.POINTER(ctypes.c_float)]
+        L.logan_autotune_save.argtypes = [p, ctypes.c_char_p]
+        L.logan_server_create.argtypes = [p, ctypes.c_size_t, ctypes.c_int, u32, ctypes.POINTER(p)]
+        L.logan_server_submit.argtypes = [p, ctypes.POINTER(RequestT), ctypes.POINTER(ctypes.c_uint64)]
+        L.logan_server_poll.argtypes = [p, ctypes.c_uint64, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_int), ctypes.POINTER(ctypes.c_double)]
+        L.logan_server_wait.argtypes = [p, ctypes.c_uint64, ctypes.c_int, ctypes.POINTER(ctypes.c_int),
+                                        ctypes.POINTER(ctypes.c_double)]
+        L.logan_server_cancel.argtypes = [p, ctypes.c_uint64]
+        L.logan_server_stats.argtypes = [p, ctypes.POINTER(ServerStatsT)]
+        L.logan_server_destroy.argtypes = [p]
+        L.logan_extend_batch_noalloc.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT),
+                                                 p, u32, i32, i32, i32, i32, p, p, p]
         L.logan_intpeak.argtypes = [ctypes.c_int, ctypes.c_int, ctypes.c_int,
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
         L.logan_set_level_table.argtypes = [p, ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
@@ -206,6 +237,29 @@ class Context:
         _check(lib().logan_get_level_table(self._h, arr, X_CLASSES), "logan_get_level_table")
         return list(arr)
 
+    def autotune(self, A: DevicePool, B: DevicePool, seeds, match=1, mismatch=-1, gap=-1, X=50,
+                 X_per_pair=None, reps: int = 2, save: Optional[str] = None):
+        """Times every start level per X class on this sample batch and keeps
+        the fastest in the context's table; returns (table, ms[class][level])."""
+        import torch
+        n = int(seeds.shape[0])
+        ws = self.workspace(A, B, n)
+        out = torch.empty((max(n, 1), 10), dtype=torch.int32, device=f"cuda:{self.device}")
+        nl = num_levels()
+        ms = (ctypes.c_float * (X_CLASSES * nl))()
+        ca, cb = A.c(), B.c()
+        stream = torch.cuda.current_stream(self.device)
+        _check(lib().logan_autotune(self._h, ctypes.byref(ca), ctypes.byref(cb), seeds.data_ptr(),
+                                    n, match, mismatch, gap, X,
+                                    X_per_pair.data_ptr() if X_per_pair is not None else None,
+                                    ws.data_ptr(), ws.numel(), out.data_ptr(),
+                                    ctypes.c_void_p(stream.cuda_stream), reps, ms),
+               "logan_autotune")
+        if save:
+            _check(lib().logan_autotune_save(self._h, save.encode()), "logan_autotune_save")
+        grid = [[ms[c * nl + l] for l in range(nl)] for c in range(X_CLASSES)]
+        return self.level_table(), grid
+
     def workspace_size(self, A: DevicePool, B: DevicePool, n_pairs: int) -> int:
         n = ctypes.c_size_t()
         ca, cb = A.c(), B.c()
@@ -268,3 +322,107 @@ def batch_to_device(b, packed2bit: Optional[bool] = None, device="cuda"):
     S = seeds_to_device(b.seeds, device)
     Xs = None if b.Xs is None else torch.from_numpy(np.ascontiguousarray(b.Xs, np.int32)).to(device)
     return A, B, S, Xs
+
+
+class HostRequest:
+    """A request's host buffers (pinned torch tensors) and its C view."""
+
+    def __init__(self, b, packed2bit: bool = True, pin: bool = True):
+        import torch
+        from . import synth
+
+        def t(a, dtype=None):
+            x = torch.from_numpy(np.ascontiguousarray(a) if dtype is None
+                                 else np.ascontiguousarray(a, dtype=dtype))
+            return x.pin_memory() if pin else x
+
+        def pool(p, off, ln):
+            bases = synth.pack2bit(p).view(np.int32) if packed2bit else p
+            return (t(bases), t(np.ascontiguousarray(off, np.uint64).view(np.int64)),
+                    t(np.ascontiguousarray(ln, np.uint32).view(np.int32)), int(p.size))
+
+        self.batch = b
+        self.n_pairs = b.n_pairs
+        self.A = pool(b.poolA, b.offA, b.lenA)
+        self.B = self.A if b.shared_pool else pool(b.poolB, b.offB, b.lenB)
+        arr = np.stack([b.seeds[f] for f in ("idxA", "idxB", "posA", "posB", "len")], axis=1)
+        self.seeds = t(arr.astype(np.uint32).view(np.int32))
+        self.Xs = None if b.Xs is None else t(b.Xs, np.int32)
+        self.results = torch.zeros((max(1, b.n_pairs), 10), dtype=torch.int32)
+        if pin:
+            self.results = self.results.pin_memory()
+        self.packed2bit = packed2bit
+
+    def _seqs(self, P) -> SeqsT:
+        bases, off, ln, nb = P
+        return SeqsT(bases.data_ptr() if bases.numel() else None,
+                     off.data_ptr() if ln.numel() else None,
+                     ln.data_ptr() if ln.numel() else None, int(ln.numel()),
+                     1 if self.packed2bit else 0, nb)
+
+    def c(self) -> RequestT:
+        b = self.batch
+        return RequestT(self._seqs(self.A), self._seqs(self.B), 1 if self.B is self.A else 0,
+                        self.seeds.data_ptr(), self.n_pairs, b.match, b.mismatch, b.gap, b.X,
+                        self.Xs.data_ptr() if self.Xs is not None else None,
+                        self.results.data_ptr())
+
+    def result_array(self) -> np.ndarray:
+        return self.results.numpy().view(RESULT_DTYPE).reshape(-1)[:self.n_pairs]
+
+
+class Server:
+    """Continuous-batching server (logan_server_t) on a context's GPU."""
+
+    def __init__(self, ctx: Context, budget_bytes: int, max_inflight: int = 4,
+                 max_queued: int = 0):
+        self._h = ctypes.c_void_p()
+        _check(lib().logan_server_create(ctx._h, int(budget_bytes), int(max_inflight),
+                                         int(max_queued), ctypes.byref(self._h)),
+               "logan_server_create")
+        self._live = {}
+
+    def submit(self, req: HostRequest) -> int:
+        t = ctypes.c_uint64()
+        creq = req.c()
+        rc = lib().logan_server_submit(self._h, ctypes.byref(creq), ctypes.byref(t))
+        _check(rc, "logan_server_submit")
+        self._live[t.value] = req  # keep host buffers alive until done
+        return t.value
+
+    def wait(self, ticket: int, timeout_ms: int = -1):
+        """(status, latency_ms); raises LoganError(ETIMEOUT) on timeout."""
+        st, lat = ctypes.c_int(), ctypes.c_double()
+        _check(lib().logan_server_wait(self._h, ticket, timeout_ms, ctypes.byref(st),
+                                       ctypes.byref(lat)), "logan_server_wait")
+        self._live.pop(ticket, None)
+        return st.value, lat.value
+
+    def poll(self, ticket: int):
+        done, st, lat = ctypes.c_int(), ctypes.c_int(), ctypes.c_double()
+        _check(lib().logan_server_poll(self._h, ticket, ctypes.byref(done), ctypes.byref(st),
+                                       ctypes.byref(lat)), "logan_server_poll")
+        if not done.value:
+            return None
+        self._live.pop(ticket, None)
+        return st.value, lat.value
+
+    def cancel(self, ticket: int):
+        _check(lib().logan_server_cancel(self._h, ticket), "logan_server_cancel")
+
+    def stats(self) -> dict:
+        st = ServerStatsT()
+        _check(lib().logan_server_stats(self._h, ctypes.byref(st)), "logan_server_stats")
+        return {f: getattr(st, f) for f, _ in ServerStatsT._fields_}
+
+    def close(self):
+        if self._h:
+            _check(lib().logan_server_destroy(self._h), "logan_server_destroy")
+            self._h = ctypes.c_void_p()
+            self._live.clear()
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

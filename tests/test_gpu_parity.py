@@ -4,6 +4,7 @@ import numpy as np
 import pytest
 
 from paper_2002_05200_gb300 import logan, synth
+from paper_2002_05200_gb300.csrc_meta import x_class
 from tests.gpu_common import assert_same, run_gpu, run_oracle
 
 pytestmark = pytest.mark.gpu
@@ -179,3 +180,27 @@ def test_timing_and_level_counts(ctx):
     # every completed extension's cells are attributed to exactly one level
     assert sum(st["cells"]) == int(g["cells"].sum())
     assert st["launches"] >= 10
+
+
+def test_autotune_table_and_roundtrip(ctx, tmp_path):
+    b = synth.uneven_batch(n_pairs=300, max_len=20_000, seed=31)
+    A, B, S, Xs = logan.batch_to_device(b, packed2bit=True)
+    before = ctx.level_table()
+    path = str(tmp_path / "tune.json")
+    table, ms = ctx.autotune(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, reps=1, save=path)
+    nl = logan.num_levels()
+    assert all(0 <= v < nl for v in table)
+    present = {x_class(int(x)) for x in b.Xs}
+    for c in range(logan.X_CLASSES):
+        if c in present:
+            assert all(t > 0 for t in ms[c]) and table[c] == int(np.argmin(ms[c]))
+        else:
+            assert all(t == -1 for t in ms[c]) and table[c] == before[c]
+    # results with the tuned table are still exact
+    ref = run_oracle(b)
+    assert_same(run_gpu(ctx, b, packed2bit=True), ref, "tuned")
+    # the saved table loads back into a new context
+    c2 = logan.Context(0, autotune_json=path)
+    assert c2.level_table() == table
+    c2.close()
+    ctx.set_level_table(before)
