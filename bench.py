@@ -53,6 +53,13 @@ def parse():
                     help="target host time of the oracle sample")
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the timed persistent steps (for profiler runs)")
+    ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--serving-rate", type=float, default=60.0, help="requests per second")
+    ap.add_argument("--serving-requests", type=int, default=240)
+    ap.add_argument("--serving-budget-gb", type=float, default=16.0)
+    ap.add_argument("--serving-inflight", type=int, default=8)
+    ap.add_argument("--serving-sweep", type=str, default="",
+                    help="comma-separated rates: print one serving JSON line per rate and exit")
     return ap.parse_args()
 
 
@@ -128,6 +135,79 @@ class ClockSampler:
                 "samples": len(sm)}
 
 
+# ---------------------------------------------------------------- serving
+def serving_run(ctx, rate: float, n_requests: int, budget_gb: float, inflight: int,
+                distinct: int = 12, seed: int = 4):
+    """Poisson arrivals of requests (log-uniform 1..10,000 pairs, uneven
+    lengths 1 kbp-1 Mbp, X = 50) drawn from a pool of `distinct` pre-built
+    requests; latency = submit -> results in host memory."""
+    import torch
+
+    from paper_2002_05200_gb300 import logan, synth
+    rng = np.random.default_rng(seed)
+    pool = [logan.HostRequest(b) for _, b in synth.serving_requests(distinct, rate, seed=seed)]
+    # reference results of each distinct request, run alone
+    alone = []
+    for h in pool:
+        A, B, S, Xs = logan.batch_to_device(h.batch, packed2bit=True)
+        o = ctx.extend(A, B, S, h.batch.match, h.batch.mismatch, h.batch.gap, h.batch.X, Xs)
+        torch.cuda.synchronize()
+        alone.append(logan.results_to_numpy(o))
+        del A, B, S, Xs, o
+    gaps = rng.exponential(1.0 / rate, size=n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    which = rng.integers(0, distinct, size=n_requests)
+    bufs = [torch.empty((max(1, pool[w].n_pairs), 10), dtype=torch.int32).pin_memory()
+            for w in which]
+    srv = logan.Server(ctx, budget_bytes=int(budget_gb * (1 << 30)), max_inflight=inflight)
+    lat = [None] * n_requests
+    done_at = [0.0] * n_requests
+    tickets = [None] * n_requests
+    ready = threading.Semaphore(0)
+
+    def waiter():
+        for k in range(n_requests):
+            ready.acquire()
+            st, ms = srv.wait(tickets[k], timeout_ms=600_000)
+            lat[k] = ms if st == 0 else None
+            done_at[k] = time.perf_counter()
+
+    th = threading.Thread(target=waiter)
+    th.start()
+    t0 = time.perf_counter()
+    for k in range(n_requests):
+        delay = t0 + arrivals[k] - time.perf_counter()
+        if delay > 0:
+            time.sleep(delay)
+        while True:
+            try:
+                tickets[k] = srv.submit(pool[which[k]], bufs[k])
+                break
+            except logan.LoganError as e:
+                if e.code != logan.EAGAIN:
+                    raise
+                time.sleep(0.001)
+        ready.release()
+    th.join()
+    t_end = max(done_at)
+    stats = srv.stats()
+    srv.close()
+    ok = all(np.array_equal(bufs[k].numpy().view(logan.RESULT_DTYPE).reshape(-1)[:pool[which[k]].n_pairs],
+                            alone[which[k]]) for k in range(n_requests))
+    good = [x for x in lat if x is not None]
+    pairs = int(sum(pool[w].n_pairs for w in which))
+    cells = int(sum(int(alone[w]["cells"].sum()) for w in which))
+    span = t_end - t0
+    return {"rate_req_s": rate, "requests": n_requests, "distinct_requests": distinct,
+            "budget_gb": budget_gb, "inflight": inflight,
+            "p50_ms": float(np.percentile(good, 50)) if good else None,
+            "p99_ms": float(np.percentile(good, 99)) if good else None,
+            "mean_pairs_per_request": pairs / n_requests,
+            "pairs_per_s": pairs / span, "gcups": cells / span / 1e9,
+            "failed": n_requests - len(good), "peak_arena_gb": stats["peak_bytes"] / (1 << 30),
+            "results_identical_to_alone": bool(ok)}
+
+
 # ---------------------------------------------------------------- CPU oracle
 def cpu_sample(b, seconds: float, threads=None):
     """Times the oracle on consecutive chunks of pairs until `seconds` of host
@@ -189,8 +269,17 @@ def main():
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
     torch.cuda.set_device(local)
 
-    from paper_2002_05200_gb300 import build as lib_build, logan
+    from paper_2002_05200_gb300 import build as lib_build, logan, shard
     lib_build.build()
+    if args.serving_sweep:
+        ctx0 = logan.Context(local)
+        for r in [float(x) for x in args.serving_sweep.split(",") if x]:
+            res = serving_run(ctx0, r, args.serving_requests, args.serving_budget_gb,
+                              args.serving_inflight)
+            if rank == 0:
+                print(json.dumps({"serving": res}), flush=True)
+        ctx0.close()
+        return
     b = workload(args.pairs, rank)
     A, B, S, Xs = logan.batch_to_device(b, packed2bit=True, device=f"cuda:{local}")
     ctx = logan.Context(local)
@@ -221,9 +310,7 @@ def main():
         barrier()
         ms = e0.elapsed_time(e1)
         if world > 1:
-            t = torch.tensor([ms], device=f"cuda:{local}")
-            dist.all_reduce(t, op=dist.ReduceOp.MAX)
-            ms = float(t.item())
+            ms, _ = shard.reduce_step(ms, 0, device=f"cuda:{local}")
         return ms / steps
 
     # persistent form, with per-level events kept for every timed step
@@ -241,9 +328,7 @@ def main():
     # rank totals
     tot_cells = cells
     if world > 1:
-        t = torch.tensor([cells], dtype=torch.float64, device=f"cuda:{local}")
-        dist.all_reduce(t)
-        tot_cells = int(t.item())
+        _, tot_cells = shard.reduce_step(0.0, cells, device=f"cuda:{local}")
     value = tot_cells / (ms * 1e-3) / 1e9
 
     # dominant kernel: the level with the most device time
@@ -319,6 +404,13 @@ def main():
         line["e2e"] = {"value": tot_cells / (ms_e2e * 1e-3) / 1e9, "unit": "GCUPS",
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "ms_per_step": ms_e2e, "results_identical": ok}
+
+    if not args.no_serving:
+        line["serving"] = serving_run(ctx, args.serving_rate, args.serving_requests,
+                                      args.serving_budget_gb, args.serving_inflight)
+        line["metric_serving"] = {"p50_ms": line["serving"]["p50_ms"],
+                                  "p99_ms": line["serving"]["p99_ms"],
+                                  "at_rate_req_s": args.serving_rate}
 
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         g, cores, pairs, ccells, dt = cpu_sample(b, args.cpu_seconds)

@@ -244,12 +244,16 @@ int logan_last_stats(logan_ctx_t *ctx, logan_stats_t *stats);
  * the counters they come from have been overwritten). */
 int logan_call_stats(logan_ctx_t *ctx, int back, logan_stats_t *stats);
 
-/* Integer-instruction throughput microbenchmark on `device` (the ALU
- * roofline's measured denominator): every thread of a grid of
- * (SMs x blocks_per_sm) blocks runs independent chains of `op` (0: 32-bit
- * add, 1: 32-bit max, 2: fused add+max) for `iters` iterations.  Writes the
- * achieved thread-instructions per second (one warp instruction = 32) and
- * the kernel time.  Synchronous; allocates and frees a small device buffer. */
+/* Instruction-throughput microbenchmark on `device` (the ALU roofline's
+ * measured denominator): 2048 threads per SM run 8 chains each of one
+ * operation `op`, every step reading a neighbouring chain: 0 int32 add,
+ * 1 int32 max, 2 int32 add+max (DPX), 3 int16x2 3-input max, 4 int16x2
+ * add+max, 5 fp32 max, 6 fp16x2 max, 7 fp16x2 add, 8 int32 multiply-add,
+ * 9 fp32 add, 10 fp32 fma, 11 3-input logic, 12 bit test + select (two
+ * instructions), 13 byte permute, 14 fp32 compare + select (two);
+ * `iters` x 128 steps per chain.  Writes the achieved thread-instructions
+ * per second (one warp instruction = 32) and the kernel time.  Synchronous;
+ * allocates and frees a small device buffer. */
 int logan_intpeak(int device, int op, int iters, double *instr_per_s, float *ms);
 
 /* Start-level table: X class -> first window level of an extension.  X

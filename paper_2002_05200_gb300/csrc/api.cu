@@ -131,8 +131,9 @@ struct DeviceGuard {
 
 void default_table(LevelTable& t) {
     // X class -> first window level.  Band width is about 0.8 X on related
-    // reads; a level needs width + cells-per-lane + 1 rows of window.
-    const int8_t lv[kXClasses] = {0, 1, 1, 2, 3, 4, 5, 6};
+    // reads (X=50: <= 59 rows, X=100: <= 100, X=500: <= 444); a level holds
+    // bands up to window - rows-per-lane - 1.
+    const int8_t lv[kXClasses] = {0, 1, 2, 2, 3, 4, 5, 6};
     for (int i = 0; i < kXClasses; ++i) t.lv[i] = lv[i];
     t.max_level = kNumLevels - 1;
     t.only_xclass = -1;

@@ -135,7 +135,8 @@ __device__ __forceinline__ int work_bucket(uint32_t m, uint32_t n) {
 __device__ __forceinline__ int item_level(const Item& it, LevelTable table, int force, int maxl) {
     const int xc = x_class(it.X);
     if (table.only_xclass >= 0 && xc != table.only_xclass) return -1;
-    const int l = force >= 0 ? force : int(table.lv[xc]);
+    int l = force >= 0 ? force : int(table.lv[xc]);
+    if (it.X > kGroupMaxX && l < kWarpLevels) l = kWarpLevels;
     return min(l, maxl);
 }
 

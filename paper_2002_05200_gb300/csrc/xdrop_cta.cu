@@ -1,5 +1,5 @@
-// X-drop extension with a multi-warp unit per extension (window levels 5
-// and 6: 128 or 512 threads x 8 cells in registers).
+// X-drop extension with a multi-warp unit per extension (window level 6:
+// 512 threads x 8 cells in registers).
 //
 // Same cell update as the one-warp kernel (paper Sec. III-A recurrence and
 // X-drop rule, Algorithm 2), with the anti-diagonal split across warps as in
@@ -271,7 +271,6 @@ __global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int l
 cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int plain,
                              cudaStream_t s) {
     switch (level) {
-        case 5: k_cta_persistent<8, 4><<<grid, 128, 0, s>>>(ka, level, plain); break;
         case 6: k_cta_persistent<8, 16><<<grid, 512, 0, s>>>(ka, level, plain); break;
         default: return cudaErrorInvalidValue;
     }
@@ -282,7 +281,6 @@ int cta_level_blocks_per_sm(int level) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (level) {
-        case 5: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cta_persistent<8, 4>, 128, 0); break;
         case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cta_persistent<8, 16>, 512, 0); break;
         default: break;
     }

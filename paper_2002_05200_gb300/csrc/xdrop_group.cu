@@ -1,0 +1,436 @@
+// X-drop extension with G-lane units, 32/G extensions per warp, band held
+// in registers (window levels 0..5).
+//
+// Method (paper Sec. III-A recurrence and X-drop rule; Algorithm 1 sweep;
+// Algorithm 2 cell update; Sec. IV-A parallel max reduction):
+//   anti-diagonal d holds cells (i, d-i).  Lane g of a unit owns rows
+//   i = base + g*C + k (k < C) of a window [base, base + W), W = G*C, that
+//   slides up in whole lanes.  The three rolling anti-diagonals (d-2, d-1,
+//   d) are three register arrays that swap roles every step (the loop is
+//   unrolled three times), so no value moves in memory:
+//     up   = S(i-1, j)   on d-1: own register k-1, or lane g-1's C-1 (shuffle)
+//     left = S(i, j-1)   on d-1: own register k
+//     diag = S(i-1, j-1) on d-2: own register k-1, or lane g-1's C-1 (shuffle)
+//
+// Scores are held relative to the pruning threshold of their anti-diagonal,
+// u = S - T_d with T_d = best_{<d} - X, so a cell is live iff u >= 0 and -inf
+// is NEGU.  Moving a value from d-1 or d-2 to d adds T_{d-1} - T_d or
+// T_{d-2} - T_d; both are folded into the per-step gap and match/mismatch
+// constants, so re-basing costs nothing per cell.  Every live cell's
+// key = u*W + (W-1-row) is reduced by one max per unit: the largest key holds
+// the anti-diagonal's best score and, for equal scores, the smallest row --
+// the best cell's tie-break without a second search.  Live rows are one warp
+// ballot; the first/last set lanes give the trimmed band (Algorithm 1's trims
+// from both ends).
+//
+// Several extensions share a warp so that the per-anti-diagonal bookkeeping
+// is paid once per warp.  Window slides, result writes and item refills run
+// once per three steps at the loop top (the window keeps three rows of slack
+// above the band), so the unrolled steps hold only the hot path.  A band that
+// outgrows the window is handed to the next, wider level, which recomputes
+// it.  Items with X > kGroupMaxX never start here (binning sends them to the
+// multi-warp levels): the keys need (X + max score) * W < 2^31.
+#include "internal.h"
+
+namespace logan {
+
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr int NEGU = -(1 << 20);  // -inf of the relative scores
+
+// 2-bit codes of a lane's C rows: 32 bits up to 16 rows, 64 bits above
+template <int C>
+struct CodeWord {
+    using T = uint32_t;
+};
+template <>
+struct CodeWord<32> {
+    using T = unsigned long long;
+};
+
+template <int G, int C>
+struct Group {
+    using Code = typename CodeWord<C>::T;
+    static constexpr int U = 32 / G;  // units per warp
+    static constexpr int W = G * C;   // window rows (a power of two)
+    static constexpr int LOG2W =
+        W == 32 ? 5 : W == 64 ? 6 : W == 128 ? 7 : W == 256 ? 8 : W == 512 ? 9 : 10;
+    static constexpr Code MASK2C = (C >= 16) ? ~Code(0) : ((Code(1) << (2 * C)) - 1u);
+    static constexpr uint32_t ALLC = (C >= 32) ? 0xffffffffu : ((1u << C) - 1u);
+    static constexpr int PREFETCH = 16 * G;  // b' codes held by a unit
+    static_assert((1 << LOG2W) == W, "window must be a power of two");
+};
+
+// Per-unit state, replicated in every lane of the unit.
+template <int C>
+struct UState {
+    int base, lo, hi, d;
+    int best, T, T1, T2;  // T = T_d for the coming step, T1 = T_{d-1}, T2 = T_{d-2}
+    int bi, bj;
+    int m, n, X;
+    unsigned long long cells;
+    int64_t apos, bpos;
+    int dir;
+    int q0;          // first b' stream index held in the unit's prefetch words
+    uint32_t bpre;   // this lane's 16 prefetched b' codes: q0 + 16*g ...
+    uint32_t item;
+    bool active;     // extension in progress
+    bool done;       // finished, result not written yet
+    bool overflow;   // finished because the band left the window
+    typename CodeWord<C>::T aw, bw;  // a' / b' codes of the lane's rows, row k at bits 2k
+};
+
+template <int C>
+__device__ __forceinline__ uint32_t a_code(const KernelArgs& ka, const UState<C>& u, int64_t q) {
+    return stream_code(ka.wa, u.apos, u.dir, uint32_t(u.m), q);
+}
+template <int C>
+__device__ __forceinline__ uint32_t b_code(const KernelArgs& ka, const UState<C>& u, int64_t q) {
+    return stream_code(ka.wb, u.bpos, u.dir, uint32_t(u.n), q);
+}
+
+// 16 consecutive codes of pool positions s..s+15 (s >= 0; the pool keeps one
+// spare word after its last base).
+__device__ __forceinline__ uint32_t load16(const uint32_t* __restrict__ w, int64_t s) {
+    const int64_t wi = s >> 4;
+    return __funnelshift_r(__ldg(w + wi), __ldg(w + wi + 1), uint32_t(s & 15) * 2u);
+}
+
+// reverses the order of the sixteen 2-bit codes of a word
+__device__ __forceinline__ uint32_t rev16(uint32_t x) {
+    x = __brev(x);
+    return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+}
+
+// b' stream codes q..q+15 in stream order (0 for indices outside [0, n)).
+template <int C>
+__device__ __forceinline__ uint32_t b_codes16(const KernelArgs& ka, const UState<C>& u, int q) {
+    if (q < 0 || q >= u.n) return 0u;
+    if (u.dir > 0) return load16(ka.wb, u.bpos + q);
+    const int64_t p = u.bpos - q;  // position of code q; codes q+t sit at p-t
+    int64_t s = p - 15;
+    uint32_t sh = 0u;
+    if (s < 0) {
+        sh = uint32_t(-s) * 2u;
+        s = 0;
+    }
+    return rev16(load16(ka.wb, s)) >> sh;
+}
+
+template <int G>
+__device__ __forceinline__ int unit_max(int v) {
+    if (G == 32) return __reduce_max_sync(FULL, v);
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o, G));
+    return v;
+}
+
+template <int G, int C>
+__device__ __forceinline__ void unit_init(const KernelArgs& ka, UState<C>& u, uint32_t id, int gl,
+                                          int (&Q2)[C], int (&Q1)[C]) {
+    const Item it = ka.items[id];
+    u.item = id;
+    u.apos = it.a_pos;
+    u.bpos = it.b_pos;
+    u.dir = (it.flags & ITEM_LEFT) ? -1 : 1;
+    u.m = int(it.m);
+    u.n = int(it.n);
+    u.X = it.X;
+    u.base = 0;
+    u.lo = 0;
+    u.hi = 0;
+    u.d = 1;
+    u.best = 0;
+    u.T = -it.X;
+    u.T1 = -it.X;
+    u.T2 = -it.X;
+    u.bi = 0;
+    u.bj = 0;
+    u.cells = 0ull;
+    u.bw = 0u;
+    u.aw = 0u;
+    u.q0 = 0;
+    u.bpre = b_codes16(ka, u, 16 * gl);
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        Q2[k] = NEGU;
+        Q1[k] = NEGU;
+        u.aw |= typename Group<G, C>::Code(a_code(ka, u, int64_t(gl) * C + k - 1)) << (2 * k);
+    }
+    if (gl == 0) Q1[0] = it.X;  // S(0,0) = 0, relative to T_0 = -X
+    const bool too_big = it.X > kGroupMaxX;  // only reachable in the plain form
+    u.active = !too_big;
+    u.done = too_big;
+    u.overflow = too_big;
+}
+
+// Result or escalation of a finished unit (its leader lane writes).
+template <int C>
+__device__ __forceinline__ void unit_finish(const KernelArgs& ka, const UState<C>& u, int level,
+                                            int gl) {
+    if (gl != 0) return;
+    if (u.overflow) {
+        const int nl = level + 1 <= int(ka.max_level) ? level + 1 : kNumLevels;
+        const unsigned int t = atomicAdd(&ka.counters->tail[nl], 1u);
+        ka.queues[size_t(nl) * ka.qcap + t] = u.item;
+    } else {
+        ExtRes r;
+        r.best = u.best;
+        r.bi = u.bi;
+        r.bj = u.bj;
+        r.status = 0;
+        r.cells = u.cells;
+        ka.ext[u.item] = r;
+        atomicAdd(&ka.counters->cells[level], u.cells);
+    }
+}
+
+// Loop top: slide windows so that the next three steps fit, and keep the b'
+// prefetch covering them.  Q2 = d-2, Q1 = d-1.
+template <int G, int C>
+__device__ __forceinline__ void unit_prepare(const KernelArgs& ka, UState<C>& u, int gl,
+                                             int (&Q2)[C], int (&Q1)[C]) {
+    using Gr = Group<G, C>;
+    const int rlo = max(u.lo, u.d - u.n);
+    const int top = min(u.hi + 3, u.m);  // highest row the next three steps can reach
+    const bool need = u.active && top >= u.base + Gr::W;
+    if (__any_sync(FULL, need)) {
+        const int s = need ? (rlo - 1 - u.base) / C : 0;
+        const bool ovf = need && (s <= 0 || top >= u.base + s * C + Gr::W);
+        const int sh = (need && !ovf) ? s : 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            Q2[k] = __shfl_down_sync(FULL, Q2[k], sh, G);
+            Q1[k] = __shfl_down_sync(FULL, Q1[k], sh, G);
+        }
+        u.aw = __shfl_down_sync(FULL, u.aw, sh, G);
+        u.bw = __shfl_down_sync(FULL, u.bw, sh, G);
+        u.base += sh * C;
+        if (sh > 0 && gl >= G - sh) {
+            const int i0 = u.base + gl * C;
+            u.aw = 0u;
+            u.bw = 0u;
+#pragma unroll
+            for (int k = 0; k < C; ++k) {
+                Q2[k] = NEGU;
+                Q1[k] = NEGU;
+                u.aw |= typename Gr::Code(a_code(ka, u, int64_t(i0) + k - 1)) << (2 * k);
+                // b' codes as of anti-diagonal d-1: index (d-1) - i - 1
+                u.bw |= typename Gr::Code(b_code(ka, u, int64_t(u.d) - 2 - (i0 + k))) << (2 * k);
+            }
+        }
+        if (ovf) {
+            u.active = false;
+            u.done = true;
+            u.overflow = true;
+        }
+    }
+    // the next three steps read b' stream indices q .. q+2
+    const int q = u.d - u.base - 1;
+    const bool refill = u.active && (q < u.q0 || q + 2 >= u.q0 + Gr::PREFETCH);
+    if (__any_sync(FULL, refill)) {
+        if (refill) {
+            u.q0 = q;
+            u.bpre = b_codes16(ka, u, q + 16 * gl);
+        }
+    }
+}
+
+// One anti-diagonal step of every unit of the warp.  Q2 = d-2, Q1 = d-1 on
+// entry (relative to T2, T1); O receives d (relative to T).  Inactive units
+// compute garbage without effects.
+template <int G, int C>
+__device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, int gl, int unit,
+                                           int (&Q2)[C], int (&Q1)[C], int (&O)[C]) {
+    using Gr = Group<G, C>;
+    const int rlo = max(u.lo, u.d - u.n);
+    const int rhi = min(u.hi + 1, u.m);
+    const bool run = u.active && rlo <= rhi;
+    // b' shift register: lane 0 takes stream index d - base - 1
+    const int qq = u.d - u.base - 1 - u.q0;
+    const uint32_t pre = __shfl_sync(FULL, u.bpre, unit * G + ((qq >> 4) & (G - 1)));
+    const uint32_t front = (pre >> (uint32_t(qq & 15) * 2u)) & 3u;
+    uint32_t carry = uint32_t(__shfl_up_sync(FULL, u.bw, 1, G) >> (2 * (C - 1))) & 3u;
+    carry = gl == 0 ? front : carry;
+    u.bw = ((u.bw << 2) | typename Gr::Code(carry)) & Gr::MASK2C;
+    int upc = __shfl_up_sync(FULL, Q1[C - 1], 1, G);
+    int dgc = __shfl_up_sync(FULL, Q2[C - 1], 1, G);
+    upc = gl == 0 ? NEGU : upc;
+    dgc = gl == 0 ? NEGU : dgc;
+    const typename Gr::Code x = u.aw ^ u.bw;
+    const typename Gr::Code eq = ~(x | (x >> 1));  // bit 2k set iff row k's bases match
+    // per-step constants: re-basing of d-1 and d-2 values onto T_d
+    const int o1 = ka.sc.gap + u.T1 - u.T;
+    const int o2 = u.T2 - u.T;
+    const int sM = ka.sc.match + o2, sMM = ka.sc.mismatch + o2;
+    // rows of this lane inside [rlo, rhi]
+    const int i0 = u.base + gl * C;
+    const int kmin = rlo - i0, kmax = rhi - i0;
+    uint32_t rb = 0u;
+    if (C >= 8) {
+        const uint32_t lom = kmin <= 0 ? Gr::ALLC : (kmin >= C ? 0u : (Gr::ALLC << kmin) & Gr::ALLC);
+        const uint32_t him = kmax >= C - 1 ? Gr::ALLC : (kmax < 0 ? 0u : Gr::ALLC >> (C - 1 - kmax));
+        rb = lom & him;
+    }
+    int lkey = NEGU * Gr::W;
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        const int up = k ? Q1[k - 1] : upc;
+        const int dg = k ? Q2[k - 1] : dgc;
+        const int t = dg + ((uint32_t(eq >> (2 * k)) & 1u) ? sM : sMM);
+        int v = __viaddmax_s32(max(up, Q1[k]), o1, t);
+        const bool inr = (C >= 8) ? ((rb >> k) & 1u) != 0u : ((k >= kmin) & (k <= kmax));
+        const bool live = inr & (v >= 0);
+        v = live ? v : NEGU;
+        O[k] = v;
+        lkey = max(lkey, v * Gr::W + (C - 1 - k));
+        bits |= live ? (1u << k) : 0u;
+    }
+    if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
+    const uint32_t vote = __ballot_sync(FULL, bits != 0u);
+    const uint32_t uv = (G == 32) ? vote : ((vote >> (unit * G)) & ((1u << G) - 1u));
+    const int wkey = unit_max<G>(lkey + (G - 1 - gl) * C);
+    const int fl = uv ? __ffs(uv) - 1 : 0, ll = uv ? 31 - __clz(uv) : 0;
+    const uint32_t fb = __shfl_sync(FULL, bits, unit * G + fl);
+    const uint32_t lb = __shfl_sync(FULL, bits, unit * G + ll);
+    if (run && uv) {
+        // best: largest key = highest relative score, smallest row on ties
+        const int umax = wkey >> Gr::LOG2W;
+        if (umax > u.X) {  // S > best  <=>  S - T_d > X
+            const int r = Gr::W - 1 - (wkey & (Gr::W - 1));
+            u.best = u.T + umax;
+            u.bi = u.base + r;
+            u.bj = u.d - u.bi;
+        }
+        u.T2 = u.T1;
+        u.T1 = u.T;
+        u.T = u.best - u.X;
+        u.lo = u.base + fl * C + __ffs(fb) - 1;
+        u.hi = u.base + ll * C + 31 - __clz(lb);
+    } else if (u.active) {
+        // empty range or no live cell: the extension ends here
+        u.active = false;
+        u.done = true;
+    }
+    u.d += 1;
+}
+
+template <int G, int C>
+__global__ void __launch_bounds__(128) k_group(KernelArgs ka, int level, int plain) {
+    using Gr = Group<G, C>;
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G, unit = lane / G;
+    const unsigned int umask = (G == 32) ? FULL : (((1u << G) - 1u) << (unit * G));
+    const unsigned int count = plain ? ka.n_items : ka.counters->tail[level];
+    const uint32_t* q = ka.queues + size_t(level) * ka.qcap;
+    // plain form: one fixed item per unit, in input order
+    const uint32_t plain_id =
+        (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * Gr::U + unit;
+    bool fresh = true;
+    int P0[C], P1[C], P2[C];
+#pragma unroll
+    for (int k = 0; k < C; ++k) {
+        P0[k] = NEGU;
+        P1[k] = NEGU;
+        P2[k] = NEGU;
+    }
+    UState<C> u;
+    u.active = false;
+    u.done = false;
+    u.overflow = false;
+    u.item = 0;
+    u.m = u.n = 0;
+    u.base = u.lo = u.hi = 0;
+    u.d = 1;
+    u.T = u.T1 = u.T2 = u.best = u.bi = u.bj = 0;
+    u.X = 0;
+    u.cells = 0ull;
+    u.apos = u.bpos = 0;
+    u.dir = 1;
+    u.q0 = 0;
+    u.bpre = u.aw = u.bw = 0u;
+    bool exhausted = false;
+    for (;;) {
+        if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
+            if (u.done) {
+                unit_finish(ka, u, level, gl);
+                u.done = false;
+            }
+            if (!u.active && !exhausted) {
+                // this unit takes its next item (lanes of the unit only)
+                uint32_t id = 0xffffffffu;
+                if (plain) {
+                    if (fresh && plain_id < count && !(ka.items[plain_id].flags & ITEM_SKIP))
+                        id = plain_id;
+                    fresh = false;
+                } else {
+                    unsigned int slot = 0u;
+                    if (gl == 0) slot = atomicAdd(&ka.counters->head[level], 1u);
+                    slot = __shfl_sync(umask, slot, unit * G);
+                    if (slot < count) id = q[slot];
+                }
+                if (id != 0xffffffffu) unit_init<G, C>(ka, u, id, gl, P0, P1);
+                else exhausted = true;
+            }
+        }
+        if (!__any_sync(FULL, u.active)) break;
+        unit_prepare<G, C>(ka, u, gl, P0, P1);
+        group_step<G, C>(ka, u, gl, unit, P0, P1, P2);
+        group_step<G, C>(ka, u, gl, unit, P1, P2, P0);
+        group_step<G, C>(ka, u, gl, unit, P2, P0, P1);
+        // roles are back to P0 = d-2, P1 = d-1
+    }
+}
+
+}  // namespace
+
+// level -> (G, C)
+#define LOGAN_GROUP_LEVELS(X) \
+    X(0, 8, 4) X(1, 8, 8) X(2, 8, 16) X(3, 16, 16) X(4, 32, 16) X(5, 32, 32)
+
+cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid,
+                                         cudaStream_t s) {
+    switch (level) {
+#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, 0); break;
+        LOGAN_GROUP_LEVELS(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_warp_level_plain(int level, const KernelArgs& ka, cudaStream_t s) {
+    int units_per_block = 0;
+    switch (level) {
+#define CASE(L, G, C) case L: units_per_block = 4 * (32 / G); break;
+        LOGAN_GROUP_LEVELS(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+    const unsigned int grid = (ka.n_items + units_per_block - 1) / units_per_block;
+    if (grid == 0) return cudaSuccess;
+    switch (level) {
+#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, 1); break;
+        LOGAN_GROUP_LEVELS(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int warp_level_blocks_per_sm(int level) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (level) {
+#define CASE(L, G, C) \
+    case L: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_group<G, C>, 128, 0); break;
+        LOGAN_GROUP_LEVELS(CASE)
+#undef CASE
+        default: break;
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+}  // namespace logan

@@ -360,12 +360,15 @@ class HostRequest:
                      ln.data_ptr() if ln.numel() else None, int(ln.numel()),
                      1 if self.packed2bit else 0, nb)
 
-    def c(self) -> RequestT:
+    def c(self, results=None) -> RequestT:
+        """C view; `results` (host int32 [n, 10]) overrides the request's own
+        result buffer so one request can be in flight several times."""
         b = self.batch
+        res = self.results if results is None else results
         return RequestT(self._seqs(self.A), self._seqs(self.B), 1 if self.B is self.A else 0,
                         self.seeds.data_ptr(), self.n_pairs, b.match, b.mismatch, b.gap, b.X,
                         self.Xs.data_ptr() if self.Xs is not None else None,
-                        self.results.data_ptr())
+                        res.data_ptr())
 
     def result_array(self) -> np.ndarray:
         return self.results.numpy().view(RESULT_DTYPE).reshape(-1)[:self.n_pairs]
@@ -382,12 +385,12 @@ class Server:
                "logan_server_create")
         self._live = {}
 
-    def submit(self, req: HostRequest) -> int:
+    def submit(self, req: HostRequest, results=None) -> int:
         t = ctypes.c_uint64()
-        creq = req.c()
+        creq = req.c(results)
         rc = lib().logan_server_submit(self._h, ctypes.byref(creq), ctypes.byref(t))
         _check(rc, "logan_server_submit")
-        self._live[t.value] = req  # keep host buffers alive until done
+        self._live[t.value] = (req, results)  # keep host buffers alive until done
         return t.value
 
     def wait(self, ticket: int, timeout_ms: int = -1):

@@ -44,7 +44,7 @@ def test_host_only_entry_points(built):
     prev = 0
     for k in range(n):
         w, t = logan.level_info(k)
-        assert w > prev and t in (32, 128, 512)
+        assert w > prev and t in (8, 16, 32, 512)
         prev = w
     with pytest.raises(logan.LoganError):
         logan.level_info(n)
