@@ -264,6 +264,15 @@ int logan_intpeak(int device, int op, int iters, double *instr_per_s, float *ms)
 int logan_set_level_table(logan_ctx_t *ctx, const int8_t *levels, int n);
 int logan_get_level_table(const logan_ctx_t *ctx, int8_t *levels, int n);
 
+/* Escalation: an extension whose band outgrows window level k continues at
+ * level next[k] (recomputed from its start; next[k] > k, and
+ * next[k] = logan_num_levels() means the global-memory fallback).  Default
+ * next[k] = k + 1, except next[2] = 5: a band outgrowing 128 rows at
+ * X <= 150 is nearly always an unrelated pair whose band keeps growing.
+ * n must be logan_num_levels(). */
+int logan_set_escalation(logan_ctx_t *ctx, const int8_t *next, int n);
+int logan_get_escalation(const logan_ctx_t *ctx, int8_t *next, int n);
+
 /* Autotuner (the paper schedules threads in proportion to X, Sec. IV-B; here
  * the unit per X class is measured): for every X class present in the
  * sample batch, runs the batch restricted to that class once per start

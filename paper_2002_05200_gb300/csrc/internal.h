@@ -23,9 +23,19 @@ struct KernelArgs {
     uint32_t n_ring_slots;
     uint32_t max_level;      // last register level before the ring
     Scoring sc;
+    // always 1; read at run time so that "x * one + y" stays a multiply-add
+    // (FMA pipe) instead of an integer add on the busier ALU pipe
+    int32_t one;
+    // level an item goes to when its band outgrows level k (kNumLevels = ring)
+    int8_t next_level[kNumLevels];
 };
 
-// extension kernels (xdrop_warp.cu / xdrop_cta.cu / xdrop_ring.cu)
+__device__ __forceinline__ int escalate(const KernelArgs& ka, int level) {
+    const int nl = ka.next_level[level];
+    return nl <= int(ka.max_level) ? nl : kNumLevels;
+}
+
+// extension kernels (xdrop_group.cu / xdrop_cta.cu / xdrop_ring.cu)
 cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid, cudaStream_t s);
 cudaError_t launch_warp_level_plain(int level, const KernelArgs& ka, cudaStream_t s);
 int warp_level_blocks_per_sm(int level);

@@ -62,19 +62,20 @@ struct Scoring {
 // Window levels: level k runs a unit of level_threads(k) threads holding
 // level_cells(k) rows each (window = threads * cells).  Levels
 // 0..kWarpLevels-1 are G-lane units (32/G extensions per warp): (G, C) =
-// (8,4) (8,8) (8,16) (16,16) (32,16) (32,32); level 6 is a 16-warp unit
-// with 8 rows per thread.  After the last level comes the global-memory
+// (8,4) (8,8) (8,16) (16,16) (32,16) (32,32); level 6 is a 4-warp unit
+// with 16 rows per thread (2048 rows), level 7 a 16-warp unit with 8 rows
+// per thread (4096 rows).  After the last level comes the global-memory
 // ring fallback (index kNumLevels).
-constexpr int kNumLevels = 7;
+constexpr int kNumLevels = 8;
 constexpr int kWarpLevels = 6;
 // largest X the G-lane levels take (their score keys need
 // (X + max score) * window < 2^31); larger X starts at level kWarpLevels
 constexpr int32_t kGroupMaxX = (1 << 20) - 4096;
 __host__ __device__ constexpr int level_cells(int k) {
-    return k == 0 ? 4 : k == 1 ? 8 : k <= 4 ? 16 : k == 5 ? 32 : 8;
+    return k == 0 ? 4 : k == 1 ? 8 : k <= 4 ? 16 : k == 5 ? 32 : k == 6 ? 16 : 8;
 }
 __host__ __device__ constexpr int level_threads(int k) {
-    return k <= 2 ? 8 : k == 3 ? 16 : k <= 5 ? 32 : 512;
+    return k <= 2 ? 8 : k == 3 ? 16 : k <= 5 ? 32 : k == 6 ? 128 : 512;
 }
 __host__ __device__ constexpr int level_window(int k) { return level_cells(k) * level_threads(k); }
 

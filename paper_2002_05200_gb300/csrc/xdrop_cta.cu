@@ -1,5 +1,5 @@
 // X-drop extension with a multi-warp unit per extension (window level 6:
-// 512 threads x 8 cells in registers).
+// 128 threads x 16 rows, level 7: 512 threads x 8 rows, in registers).
 //
 // Same cell update as the one-warp kernel (paper Sec. III-A recurrence and
 // X-drop rule, Algorithm 2), with the anti-diagonal split across warps as in
@@ -254,7 +254,7 @@ __global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int l
         const bool ovf = cta_extend<C, NW>(e, r, sm);
         if (threadIdx.x == 0) {
             if (ovf) {
-                const int nl = level + 1 <= int(ka.max_level) ? level + 1 : kNumLevels;
+                const int nl = escalate(ka, level);
                 const unsigned int tl = atomicAdd(&ka.counters->tail[nl], 1u);
                 ka.queues[size_t(nl) * ka.qcap + tl] = id;
             } else {
@@ -271,7 +271,8 @@ __global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int l
 cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int plain,
                              cudaStream_t s) {
     switch (level) {
-        case 6: k_cta_persistent<8, 16><<<grid, 512, 0, s>>>(ka, level, plain); break;
+        case 6: k_cta_persistent<16, 4><<<grid, 128, 0, s>>>(ka, level, plain); break;
+        case 7: k_cta_persistent<8, 16><<<grid, 512, 0, s>>>(ka, level, plain); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();
@@ -281,7 +282,8 @@ int cta_level_blocks_per_sm(int level) {
     int n = 0;
     cudaError_t e = cudaErrorInvalidValue;
     switch (level) {
-        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cta_persistent<8, 16>, 512, 0); break;
+        case 6: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cta_persistent<16, 4>, 128, 0); break;
+        case 7: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_cta_persistent<8, 16>, 512, 0); break;
         default: break;
     }
     return e == cudaSuccess ? n : 0;

@@ -171,7 +171,7 @@ __device__ __forceinline__ void unit_finish(const KernelArgs& ka, const UState<C
                                             int gl) {
     if (gl != 0) return;
     if (u.overflow) {
-        const int nl = level + 1 <= int(ka.max_level) ? level + 1 : kNumLevels;
+        const int nl = escalate(ka, level);
         const unsigned int t = atomicAdd(&ka.counters->tail[nl], 1u);
         ka.queues[size_t(nl) * ka.qcap + t] = u.item;
     } else {
@@ -273,21 +273,39 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
         const uint32_t him = kmax >= C - 1 ? Gr::ALLC : (kmax < 0 ? 0u : Gr::ALLC >> (C - 1 - kmax));
         rb = lom & him;
     }
+    // Per row: v = max(up + o1, left + o1, diag + sub); the additions run as
+    // multiply-adds (FMA pipe), the 3-way max is one DPX instruction, and
+    // g = (d-1 value) + o1 of row k serves as "left" of row k and "up" of
+    // row k+1.
+    const int one = ka.one;
+    const int wscale = one * Gr::W;  // a run-time W keeps the key a multiply-add
+    int gp = upc * one + o1;
     int lkey = NEGU * Gr::W;
-    uint32_t bits = 0u;
+    // dead-row bits, collected by shifting in each row's sign (dead rows hold
+    // NEGU < 0): after the loop bit C-1-k is set iff row k is dead
+    uint32_t dead = 0u;
 #pragma unroll
-    for (int k = 0; k < C; ++k) {
-        const int up = k ? Q1[k - 1] : upc;
-        const int dg = k ? Q2[k - 1] : dgc;
-        const int t = dg + ((uint32_t(eq >> (2 * k)) & 1u) ? sM : sMM);
-        int v = __viaddmax_s32(max(up, Q1[k]), o1, t);
-        const bool inr = (C >= 8) ? ((rb >> k) & 1u) != 0u : ((k >= kmin) & (k <= kmax));
-        const bool live = inr & (v >= 0);
-        v = live ? v : NEGU;
-        O[k] = v;
-        lkey = max(lkey, v * Gr::W + (C - 1 - k));
-        bits |= live ? (1u << k) : 0u;
+    for (int k = 0; k < C; k += 2) {
+        int key[2];
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+            const int kk = k + h;
+            const int g = Q1[kk] * one + o1;
+            const int dg = kk ? Q2[kk - 1] : dgc;
+            const bool match = (eq & (typename Gr::Code(1) << (2 * kk))) != typename Gr::Code(0);
+            const int t = dg * one + (match ? sM : sMM);
+            int v = __vimax3_s32(gp, g, t);
+            gp = g;
+            const bool inr = (C >= 8) ? (rb & (1u << kk)) != 0u : ((kk >= kmin) & (kk <= kmax));
+            v = (inr & (v >= 0)) ? v : NEGU;
+            O[kk] = v;
+            key[h] = v * wscale + (C - 1 - kk);
+            dead = __funnelshift_l(uint32_t(v), dead, 1);
+        }
+        lkey = __vimax3_s32(lkey, key[0], key[1]);
     }
+    // live rows of this lane; bit C-1-k <-> row k
+    const uint32_t bits = ~dead & Gr::ALLC;
     if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
     const uint32_t vote = __ballot_sync(FULL, bits != 0u);
     const uint32_t uv = (G == 32) ? vote : ((vote >> (unit * G)) & ((1u << G) - 1u));
@@ -295,6 +313,7 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
     const int fl = uv ? __ffs(uv) - 1 : 0, ll = uv ? 31 - __clz(uv) : 0;
     const uint32_t fb = __shfl_sync(FULL, bits, unit * G + fl);
     const uint32_t lb = __shfl_sync(FULL, bits, unit * G + ll);
+    // first live row of lane fl: highest set bit; last of lane ll: lowest
     if (run && uv) {
         // best: largest key = highest relative score, smallest row on ties
         const int umax = wkey >> Gr::LOG2W;
@@ -307,8 +326,8 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
         u.T2 = u.T1;
         u.T1 = u.T;
         u.T = u.best - u.X;
-        u.lo = u.base + fl * C + __ffs(fb) - 1;
-        u.hi = u.base + ll * C + 31 - __clz(lb);
+        u.lo = u.base + fl * C + (C - 1) - (31 - __clz(fb));
+        u.hi = u.base + ll * C + (C - 1) - (__ffs(lb) - 1);
     } else if (u.active) {
         // empty range or no live cell: the extension ends here
         u.active = false;

@@ -33,7 +33,8 @@ EXPORTED = ["logan_version", "logan_strerror", "logan_ctx_create", "logan_ctx_de
             "logan_set_option", "logan_get_option", "logan_num_levels", "logan_level_info",
             "logan_last_stats", "logan_call_stats", "logan_set_level_table",
             "logan_get_level_table", "logan_intpeak", "logan_autotune", "logan_autotune_save",
-            "logan_extend_batch_noalloc", "logan_server_create", "logan_server_submit",
+            "logan_extend_batch_noalloc", "logan_set_escalation", "logan_get_escalation",
+            "logan_server_create", "logan_server_submit",
             "logan_server_poll", "logan_server_wait", "logan_server_cancel", "logan_server_stats",
             "logan_server_destroy"]
 
@@ -121,6 +122,8 @@ def lib():
                                     ctypes.POINTER(ctypes.c_double), ctypes.POINTER(ctypes.c_float)]
         L.logan_set_level_table.argtypes = [p, ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
         L.logan_get_level_table.argtypes = [p, ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
+        L.logan_set_escalation.argtypes = [p, ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
+        L.logan_get_escalation.argtypes = [p, ctypes.POINTER(ctypes.c_int8), ctypes.c_int]
         _lib = L
     return _lib
 
@@ -259,6 +262,17 @@ class Context:
             _check(lib().logan_autotune_save(self._h, save.encode()), "logan_autotune_save")
         grid = [[ms[c * nl + l] for l in range(nl)] for c in range(X_CLASSES)]
         return self.level_table(), grid
+
+    def set_escalation(self, nxt):
+        n = num_levels()
+        arr = (ctypes.c_int8 * n)(*[int(v) for v in nxt])
+        _check(lib().logan_set_escalation(self._h, arr, n), "logan_set_escalation")
+
+    def escalation(self):
+        n = num_levels()
+        arr = (ctypes.c_int8 * n)()
+        _check(lib().logan_get_escalation(self._h, arr, n), "logan_get_escalation")
+        return list(arr)
 
     def workspace_size(self, A: DevicePool, B: DevicePool, n_pairs: int) -> int:
         n = ctypes.c_size_t()

@@ -40,11 +40,11 @@ def test_host_only_entry_points(built):
     assert logan.strerror(logan.EINVAL).startswith("invalid")
     assert logan.strerror(logan.ERANGE)
     n = logan.num_levels()
-    assert n == 7
+    assert n == 8
     prev = 0
     for k in range(n):
         w, t = logan.level_info(k)
-        assert w > prev and t in (8, 16, 32, 512)
+        assert w > prev and t in (8, 16, 32, 128, 512)
         prev = w
     with pytest.raises(logan.LoganError):
         logan.level_info(n)

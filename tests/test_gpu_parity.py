@@ -60,7 +60,7 @@ def test_tiny_edge_cases(ctx, seed):
     assert_same(run_gpu(ctx, b, packed2bit=True, plain=True), ref, "plain")
 
 
-@pytest.mark.parametrize("level", range(7))
+@pytest.mark.parametrize("level", range(8))
 def test_every_window_level(ctx, level):
     # each level started directly; narrower bands stay, wider ones escalate
     b = synth.uneven_batch(n_pairs=120, max_len=12_000, seed=21)
@@ -204,3 +204,20 @@ def test_autotune_table_and_roundtrip(ctx, tmp_path):
     assert c2.level_table() == table
     c2.close()
     ctx.set_level_table(before)
+
+
+def test_escalation_policies(ctx):
+    # skipping levels changes only the speed, never the results
+    b = synth.lognormal_batch(n_pairs=200, seed=17)
+    ref = run_oracle(b)
+    n = logan.num_levels()
+    default = ctx.escalation()
+    assert all(default[k] > k for k in range(n)) and default[n - 1] == n
+    for policy in ([2, 5, 5, 5, 5, 6, 8, 8], [n] * n, [1, 2, 5, 5, 6, 6, 7, 8]):
+        ctx.set_escalation(policy)
+        assert ctx.escalation() == policy
+        assert_same(run_gpu(ctx, b, packed2bit=True), ref, str(policy))
+        assert_same(run_gpu(ctx, b, packed2bit=True, plain=True), ref, "plain " + str(policy))
+    with pytest.raises(logan.LoganError):
+        ctx.set_escalation([0] * n)
+    ctx.set_escalation(default)
