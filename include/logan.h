@@ -170,7 +170,8 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  * memory is one static device array of LOGAN_NOALLOC_SCRATCH_BYTES that
  * every GPU loading the library holds until the process exits.
  *   - No cudaMalloc/cudaFree or other allocating call, and no CUDA graph is
- *     built (the context's graph option is ignored for this call).
+ *     built (the context's graph option is ignored for this call), and no
+ *     band-state records are kept (LOGAN_OPT_MIGRATION_MB is 0 for the call).
  *   - The fallback window for very wide bands is LOGAN_NOALLOC_RING_ROWS
  *     rows (wider bands give LOGAN_ERANGE for that pair).
  *   - A batch whose scratch need (logan_workspace_size with that window)
@@ -204,6 +205,8 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   LOGAN_OPT_RING_CAP      log2 of the fallback window in cells (10..22,
  *                           default 16); changes the workspace size
  *   LOGAN_OPT_PLAIN_LEVEL   window level of the plain form (default 1)
+ *   LOGAN_OPT_DEVICE        (read-only) the context's device
+ *   LOGAN_OPT_MIGRATION_MB  band-state migration budget (below)
  */
 #define LOGAN_OPT_GRAPHS 1
 #define LOGAN_OPT_TIMING 2
@@ -212,6 +215,10 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
 #define LOGAN_OPT_RING_CAP 5
 #define LOGAN_OPT_PLAIN_LEVEL 6
 #define LOGAN_OPT_DEVICE 7       /* read-only: the context's CUDA device */
+#define LOGAN_OPT_MIGRATION_MB 8 /* MiB of band-state records per window level
+                                    (default 64; 0: an overflowing extension
+                                    restarts at the next level instead of
+                                    resuming); changes the workspace size */
 int logan_set_option(logan_ctx_t *ctx, int option, int64_t value);
 int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
 
@@ -228,7 +235,9 @@ int logan_level_info(int level, int *window_cells, int *threads_per_unit);
  *   total_ms     the whole pipeline of the call;
  *   items[k]     extensions that ran at level k (started there or escalated
  *                into it);
- *   cells[k]     computed cells of the extensions that completed at level k;
+ *   cells[k]     cells computed by level k (an extension that resumes at a
+ *                wider level counts there only the cells it adds; one that
+ *                restarts there counts its repeated cells again);
  *   launches     kernels the call launched. */
 #define LOGAN_MAX_LEVELS 8
 typedef struct {
@@ -265,11 +274,10 @@ int logan_set_level_table(logan_ctx_t *ctx, const int8_t *levels, int n);
 int logan_get_level_table(const logan_ctx_t *ctx, int8_t *levels, int n);
 
 /* Escalation: an extension whose band outgrows window level k continues at
- * level next[k] (recomputed from its start; next[k] > k, and
+ * level next[k] (resuming from its saved band, or recomputed from its start
+ * when the migration records of level k are used up; next[k] > k, and
  * next[k] = logan_num_levels() means the global-memory fallback).  Default
- * next[k] = k + 1, except next[2] = 5: a band outgrowing 128 rows at
- * X <= 150 is nearly always an unrelated pair whose band keeps growing.
- * n must be logan_num_levels(). */
+ * next[k] = k + 1.  n must be logan_num_levels(). */
 int logan_set_escalation(logan_ctx_t *ctx, const int8_t *next, int n);
 int logan_get_escalation(const logan_ctx_t *ctx, int8_t *next, int n);
 

@@ -28,7 +28,23 @@ struct KernelArgs {
     int32_t one;
     // level an item goes to when its band outgrows level k (kNumLevels = ring)
     int8_t next_level[kNumLevels];
+    // migration records written by level k (nullptr or cap 0: restart instead)
+    int32_t* mig_pool[kNumLevels];
+    uint32_t mig_cap[kNumLevels];
+    int32_t* mig_slot;  // per item: (level << 24) | record, or -1
 };
+
+__device__ __forceinline__ int32_t* mig_record(const KernelArgs& ka, int32_t slot) {
+    const int lv = slot >> 24;
+    return ka.mig_pool[lv] + size_t(slot & 0xffffff) * size_t(mig_stride(lv));
+}
+
+// A record slot of `level`, or -1 when its pool is full (the item restarts).
+__device__ __forceinline__ int32_t mig_alloc(const KernelArgs& ka, int level) {
+    if (ka.mig_pool[level] == nullptr || ka.mig_cap[level] == 0) return -1;
+    const unsigned int idx = atomicAdd(&ka.counters->mig_used[level], 1u);
+    return idx < ka.mig_cap[level] ? int32_t((unsigned(level) << 24) | idx) : -1;
+}
 
 __device__ __forceinline__ int escalate(const KernelArgs& ka, int level) {
     const int nl = ka.next_level[level];
@@ -59,7 +75,7 @@ cudaError_t launch_pack(const PoolDev& p, uint32_t* words_out, cudaStream_t s);
 cudaError_t launch_validate(const PoolDev& p, cudaStream_t s);
 cudaError_t launch_split(const PoolDev& A, const PoolDev& B, const void* seeds, uint32_t n_pairs,
                          Scoring sc, int32_t X, const int32_t* Xs, Item* items, PairInfo* info,
-                         ExtRes* ext, cudaStream_t s);
+                         ExtRes* ext, int32_t* mig_slot, cudaStream_t s);
 constexpr int kBuckets = 128;
 // X class -> starting window level (the autotune table), plus the highest
 // register level in use and an optional X-class filter (-1 = all classes).

@@ -86,8 +86,25 @@ struct Counters {
     unsigned int head[kNumLevels + 1];
     unsigned int started[kNumLevels + 1];   // items that began at this level (binning)
     unsigned int pad;
-    unsigned long long cells[kNumLevels + 1];  // cells of extensions completed at each level
+    unsigned long long cells[kNumLevels + 1];  // cells computed by each level
+    unsigned int mig_used[kNumLevels];         // migration records written per level
 };
+
+// Band-state migration.  A unit whose band outgrows its window writes its
+// last two anti-diagonals (rows [base, base + rows)) and its scalars to a
+// record in HBM; the level it escalates to resumes from there instead of
+// recomputing the extension.  Record = kMigHeader int32 header + d-1 rows +
+// d-2 rows.  RELATIVE records hold scores minus the threshold of their
+// anti-diagonal (T1 for d-1, T2 for d-2; -inf = any negative value),
+// ABSOLUTE records hold scores (-inf = NEG).
+constexpr int kMigHeader = 16;
+enum MigField {
+    MIG_KIND = 0, MIG_ROWS, MIG_D, MIG_BASE, MIG_LO, MIG_HI, MIG_BEST, MIG_T, MIG_T1, MIG_T2,
+    MIG_BI, MIG_BJ, MIG_CELLS_LO, MIG_CELLS_HI, MIG_LEVEL
+};
+constexpr int MIG_RELATIVE = 1;
+constexpr int MIG_ABSOLUTE = 2;
+__host__ __device__ constexpr int mig_stride(int level) { return kMigHeader + 2 * level_window(level); }
 
 // One 2-bit code of a pool (p must lie inside the pool).
 __device__ __forceinline__ uint32_t code_at(const uint32_t* __restrict__ w, int64_t p) {

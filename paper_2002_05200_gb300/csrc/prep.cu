@@ -71,9 +71,11 @@ struct PoolView {
 __global__ void k_split(PoolView A, PoolView B, const uint32_t* __restrict__ seeds,
                         uint32_t n_pairs, Scoring sc, int32_t X, const int32_t* __restrict__ Xs,
                         Item* __restrict__ items, PairInfo* __restrict__ info,
-                        ExtRes* __restrict__ ext) {
+                        ExtRes* __restrict__ ext, int32_t* __restrict__ mig_slot) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
+    mig_slot[2 * p] = -1;
+    mig_slot[2 * p + 1] = -1;
     const uint32_t idxA = seeds[5 * p], idxB = seeds[5 * p + 1];
     const uint32_t posA = seeds[5 * p + 2], posB = seeds[5 * p + 3], k = seeds[5 * p + 4];
     const int32_t x = Xs ? Xs[p] : X;
@@ -183,6 +185,7 @@ __global__ void k_bin_scan(uint32_t* __restrict__ hist, Counters* __restrict__ c
         c->head[t] = 0u;
         c->cells[t] = 0ull;
     }
+    if (t < kNumLevels) c->mig_used[t] = 0u;
     if (t == 0) {
         c->tail[kNumLevels] = 0u;
         c->started[kNumLevels] = 0u;
@@ -210,6 +213,7 @@ __global__ void k_reset_counters(Counters* c, uint32_t first_items, int first_le
         c->started[t] = (t == first_level) ? first_items : 0u;
         c->cells[t] = 0ull;
     }
+    if (t < kNumLevels) c->mig_used[t] = 0u;
 }
 
 struct ResultOut {
@@ -264,12 +268,12 @@ cudaError_t launch_validate(const PoolDev& p, cudaStream_t s) {
 
 cudaError_t launch_split(const PoolDev& A, const PoolDev& B, const void* seeds, uint32_t n_pairs,
                          Scoring sc, int32_t X, const int32_t* Xs, Item* items, PairInfo* info,
-                         ExtRes* ext, cudaStream_t s) {
+                         ExtRes* ext, int32_t* mig_slot, cudaStream_t s) {
     if (n_pairs == 0) return cudaSuccess;
     PoolView a = {A.offsets, A.lengths, A.bad, A.words, A.count};
     PoolView b = {B.offsets, B.lengths, B.bad, B.words, B.count};
     k_split<<<blocks_for(n_pairs, 128), 128, 0, s>>>(a, b, static_cast<const uint32_t*>(seeds), n_pairs,
-                                                     sc, X, Xs, items, info, ext);
+                                                     sc, X, Xs, items, info, ext, mig_slot);
     return cudaGetLastError();
 }
 

@@ -44,14 +44,21 @@ struct CtaSmem {
     uint32_t btop[2][NW];      // per warp: b' codes of the top lane (index d % 2)
     int xbuf[(2 * C + 2) * NW * 32];  // window-slide exchange, [field][thread]
     unsigned int slot;
+    int mslot;
 };
 
 struct CState {
     int base, lo, hi, d;
     int best, bi, bj;
     unsigned long long cells;
+    unsigned long long cells0;  // cells computed before this level (resumed items)
     uint32_t aw, bw;
     bool overflow;
+    bool migrated;
+    // for saving the band on overflow
+    const KernelArgs* ka;
+    uint32_t item;
+    int level;
 };
 
 __device__ __forceinline__ int mod3(int v) { return v % 3; }
@@ -69,6 +76,34 @@ __device__ __forceinline__ bool cta_step(const ExtArgs& e, CState& st, CtaSmem<C
     if (rhi >= st.base + W) {
         const int s = (rlo - 1 - st.base) / C;
         if (s <= 0 || rhi >= st.base + s * C + W) {
+            // save rows [base, base + W) of d-1 and d-2 for the next level
+            if (t == 0) sm.mslot = mig_alloc(*st.ka, st.level);
+            __syncthreads();
+            const int32_t slot = sm.mslot;
+            if (slot >= 0) {
+                int32_t* rec = mig_record(*st.ka, slot);
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    rec[kMigHeader + t * C + k] = Q1[k];
+                    rec[kMigHeader + W + t * C + k] = Q2[k];
+                }
+                if (t == 0) {
+                    rec[MIG_KIND] = MIG_ABSOLUTE;
+                    rec[MIG_ROWS] = W;
+                    rec[MIG_D] = d;
+                    rec[MIG_BASE] = st.base;
+                    rec[MIG_LO] = st.lo;
+                    rec[MIG_HI] = st.hi;
+                    rec[MIG_BEST] = st.best;
+                    rec[MIG_BI] = st.bi;
+                    rec[MIG_BJ] = st.bj;
+                    rec[MIG_CELLS_LO] = int32_t(uint32_t(st.cells));
+                    rec[MIG_CELLS_HI] = int32_t(uint32_t(st.cells >> 32));
+                    rec[MIG_LEVEL] = st.level;
+                    st.ka->mig_slot[st.item] = slot;
+                }
+            }
+            st.migrated = slot >= 0;
             st.overflow = true;
             return true;
         }
@@ -180,34 +215,76 @@ __device__ __forceinline__ bool cta_step(const ExtArgs& e, CState& st, CtaSmem<C
 }
 
 template <int C, int NW>
-__device__ bool cta_extend(const ExtArgs& e, ExtRes& r, CtaSmem<C, NW>& sm) {
+__device__ bool cta_extend(const KernelArgs& ka, uint32_t id, int level, const ExtArgs& e,
+                           ExtRes& r, unsigned long long& cells_here, CtaSmem<C, NW>& sm) {
+    constexpr int NT = NW * 32;
     const int t = threadIdx.x, lane = t & 31, w = t >> 5;
     int P0[C], P1[C], P2[C];
-#pragma unroll
-    for (int k = 0; k < C; ++k) {
-        P0[k] = NEG;
-        P1[k] = NEG;
-        P2[k] = NEG;
-    }
-    if (t == 0) P1[0] = 0;
     CState st;
-    st.base = 0;
-    st.lo = 0;
-    st.hi = 0;
-    st.d = 1;
-    st.best = 0;
-    st.bi = 0;
-    st.bj = 0;
-    st.cells = 0ull;
+    st.ka = &ka;
+    st.item = id;
+    st.level = level;
     st.overflow = false;
+    st.migrated = false;
     st.aw = 0u;
     st.bw = 0u;
+    const int32_t slot = ka.mig_slot[id];
+    const int32_t* rec = slot >= 0 ? mig_record(ka, slot) : nullptr;
+    if (rec) {
+        // resume a band saved by a narrower level
+        const bool rel = rec[MIG_KIND] == MIG_RELATIVE;
+        const int rows = rec[MIG_ROWS];
+        const int T1 = rec[MIG_T1], T2 = rec[MIG_T2];
+        st.d = rec[MIG_D];
+        st.base = rec[MIG_BASE];
+        st.lo = rec[MIG_LO];
+        st.hi = rec[MIG_HI];
+        st.best = rec[MIG_BEST];
+        st.bi = rec[MIG_BI];
+        st.bj = rec[MIG_BJ];
+        st.cells = (unsigned long long)uint32_t(rec[MIG_CELLS_LO]) |
+                   ((unsigned long long)uint32_t(rec[MIG_CELLS_HI]) << 32);
+        const int i0 = st.base + t * C;
 #pragma unroll
-    for (int k = 0; k < C; ++k) st.aw |= a_code(e, int64_t(t) * C + k - 1) << (2 * k);
+        for (int k = 0; k < C; ++k) {
+            const int rr = t * C + k;
+            int v1 = rr < rows ? rec[kMigHeader + rr] : NEG;
+            int v2 = rr < rows ? rec[kMigHeader + rows + rr] : NEG;
+            if (rel) {
+                v1 = (rr < rows && v1 >= 0) ? v1 + T1 : NEG;
+                v2 = (rr < rows && v2 >= 0) ? v2 + T2 : NEG;
+            }
+            P1[k] = v1;
+            P0[k] = v2;
+            P2[k] = NEG;
+            st.aw |= a_code(e, int64_t(i0) + k - 1) << (2 * k);
+            st.bw |= b_code(e, int64_t(st.d) - 2 - (i0 + k)) << (2 * k);
+        }
+        (void)NT;
+    } else {
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            P0[k] = NEG;
+            P1[k] = NEG;
+            P2[k] = NEG;
+        }
+        if (t == 0) P1[0] = 0;
+        st.base = 0;
+        st.lo = 0;
+        st.hi = 0;
+        st.d = 1;
+        st.best = 0;
+        st.bi = 0;
+        st.bj = 0;
+        st.cells = 0ull;
+#pragma unroll
+        for (int k = 0; k < C; ++k) st.aw |= a_code(e, int64_t(t) * C + k - 1) << (2 * k);
+    }
+    st.cells0 = st.cells;
     if (lane == 31) {
-        sm.top[0][w] = P1[C - 1];  // d = 0
-        sm.top[2][w] = NEG;        // d = -1
-        sm.btop[0][w] = 0u;
+        sm.top[mod3(st.d + 2)][w] = P1[C - 1];  // d-1
+        sm.top[mod3(st.d + 1)][w] = P0[C - 1];  // d-2
+        sm.btop[(st.d + 1) & 1][w] = st.bw;     // codes as of d-1
     }
     __syncthreads();
     for (;;) {
@@ -220,6 +297,8 @@ __device__ bool cta_extend(const ExtArgs& e, ExtRes& r, CtaSmem<C, NW>& sm) {
     r.bj = st.bj;
     r.status = 0;
     r.cells = st.cells;
+    // cells computed here (none are kept when a band restarts elsewhere)
+    cells_here = (!st.overflow || st.migrated) ? st.cells - st.cells0 : 0ull;
     return st.overflow;
 }
 
@@ -251,15 +330,16 @@ __global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int l
         e.mismatch = ka.sc.mismatch;
         e.gap = ka.sc.gap;
         ExtRes r;
-        const bool ovf = cta_extend<C, NW>(e, r, sm);
+        unsigned long long cells_here = 0ull;
+        const bool ovf = cta_extend<C, NW>(ka, id, level, e, r, cells_here, sm);
         if (threadIdx.x == 0) {
+            if (cells_here) atomicAdd(&ka.counters->cells[level], cells_here);
             if (ovf) {
                 const int nl = escalate(ka, level);
                 const unsigned int tl = atomicAdd(&ka.counters->tail[nl], 1u);
                 ka.queues[size_t(nl) * ka.qcap + tl] = id;
             } else {
                 ka.ext[id] = r;
-                atomicAdd(&ka.counters->cells[level], r.cells);
             }
         }
         __syncthreads();

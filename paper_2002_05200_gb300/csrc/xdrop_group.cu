@@ -70,6 +70,7 @@ struct UState {
     int bi, bj;
     int m, n, X;
     unsigned long long cells;
+    unsigned long long cells0;  // cells computed before this level (resumed items)
     int64_t apos, bpos;
     int dir;
     int q0;          // first b' stream index held in the unit's prefetch words
@@ -78,6 +79,7 @@ struct UState {
     bool active;     // extension in progress
     bool done;       // finished, result not written yet
     bool overflow;   // finished because the band left the window
+    bool migrated;   // the overflowing band was saved for the next level
     typename CodeWord<C>::T aw, bw;  // a' / b' codes of the lane's rows, row k at bits 2k
 };
 
@@ -129,6 +131,7 @@ __device__ __forceinline__ int unit_max(int v) {
 template <int G, int C>
 __device__ __forceinline__ void unit_init(const KernelArgs& ka, UState<C>& u, uint32_t id, int gl,
                                           int (&Q2)[C], int (&Q1)[C]) {
+    using Code = typename Group<G, C>::Code;
     const Item it = ka.items[id];
     u.item = id;
     u.apos = it.a_pos;
@@ -137,32 +140,66 @@ __device__ __forceinline__ void unit_init(const KernelArgs& ka, UState<C>& u, ui
     u.m = int(it.m);
     u.n = int(it.n);
     u.X = it.X;
-    u.base = 0;
-    u.lo = 0;
-    u.hi = 0;
-    u.d = 1;
-    u.best = 0;
-    u.T = -it.X;
-    u.T1 = -it.X;
-    u.T2 = -it.X;
-    u.bi = 0;
-    u.bj = 0;
-    u.cells = 0ull;
     u.bw = 0u;
     u.aw = 0u;
-    u.q0 = 0;
-    u.bpre = b_codes16(ka, u, 16 * gl);
+    const int32_t slot = ka.mig_slot[id];
+    const int32_t* rec = slot >= 0 ? mig_record(ka, slot) : nullptr;
+    if (rec && rec[MIG_KIND] == MIG_RELATIVE) {
+        // resume a band saved by a narrower level
+        const int rows = rec[MIG_ROWS];
+        u.d = rec[MIG_D];
+        u.base = rec[MIG_BASE];
+        u.lo = rec[MIG_LO];
+        u.hi = rec[MIG_HI];
+        u.best = rec[MIG_BEST];
+        u.T = rec[MIG_T];
+        u.T1 = rec[MIG_T1];
+        u.T2 = rec[MIG_T2];
+        u.bi = rec[MIG_BI];
+        u.bj = rec[MIG_BJ];
+        u.cells = (unsigned long long)uint32_t(rec[MIG_CELLS_LO]) |
+                  ((unsigned long long)uint32_t(rec[MIG_CELLS_HI]) << 32);
+        u.cells0 = u.cells;
+        const int i0 = u.base + gl * C;
 #pragma unroll
-    for (int k = 0; k < C; ++k) {
-        Q2[k] = NEGU;
-        Q1[k] = NEGU;
-        u.aw |= typename Group<G, C>::Code(a_code(ka, u, int64_t(gl) * C + k - 1)) << (2 * k);
+        for (int k = 0; k < C; ++k) {
+            const int r = gl * C + k;
+            Q1[k] = r < rows ? rec[kMigHeader + r] : NEGU;
+            Q2[k] = r < rows ? rec[kMigHeader + rows + r] : NEGU;
+            u.aw |= Code(a_code(ka, u, int64_t(i0) + k - 1)) << (2 * k);
+            // b' codes as of anti-diagonal d-1: index (d-1) - i - 1
+            u.bw |= Code(b_code(ka, u, int64_t(u.d) - 2 - (i0 + k))) << (2 * k);
+        }
+        u.q0 = -(1 << 30);  // forces a prefetch refill at the loop top
+        u.bpre = 0u;
+    } else {
+        u.base = 0;
+        u.lo = 0;
+        u.hi = 0;
+        u.d = 1;
+        u.best = 0;
+        u.T = -it.X;
+        u.T1 = -it.X;
+        u.T2 = -it.X;
+        u.bi = 0;
+        u.bj = 0;
+        u.cells = 0ull;
+        u.cells0 = 0ull;
+        u.q0 = 0;
+        u.bpre = b_codes16(ka, u, 16 * gl);
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            Q2[k] = NEGU;
+            Q1[k] = NEGU;
+            u.aw |= Code(a_code(ka, u, int64_t(gl) * C + k - 1)) << (2 * k);
+        }
+        if (gl == 0) Q1[0] = it.X;  // S(0,0) = 0, relative to T_0 = -X
     }
-    if (gl == 0) Q1[0] = it.X;  // S(0,0) = 0, relative to T_0 = -X
     const bool too_big = it.X > kGroupMaxX;  // only reachable in the plain form
     u.active = !too_big;
     u.done = too_big;
     u.overflow = too_big;
+    u.migrated = false;
 }
 
 // Result or escalation of a finished unit (its leader lane writes).
@@ -171,6 +208,7 @@ __device__ __forceinline__ void unit_finish(const KernelArgs& ka, const UState<C
                                             int gl) {
     if (gl != 0) return;
     if (u.overflow) {
+        if (u.migrated) atomicAdd(&ka.counters->cells[level], u.cells - u.cells0);
         const int nl = escalate(ka, level);
         const unsigned int t = atomicAdd(&ka.counters->tail[nl], 1u);
         ka.queues[size_t(nl) * ka.qcap + t] = u.item;
@@ -182,15 +220,15 @@ __device__ __forceinline__ void unit_finish(const KernelArgs& ka, const UState<C
         r.status = 0;
         r.cells = u.cells;
         ka.ext[u.item] = r;
-        atomicAdd(&ka.counters->cells[level], u.cells);
+        atomicAdd(&ka.counters->cells[level], u.cells - u.cells0);
     }
 }
 
 // Loop top: slide windows so that the next three steps fit, and keep the b'
 // prefetch covering them.  Q2 = d-2, Q1 = d-1.
 template <int G, int C>
-__device__ __forceinline__ void unit_prepare(const KernelArgs& ka, UState<C>& u, int gl,
-                                             int (&Q2)[C], int (&Q1)[C]) {
+__device__ __forceinline__ void unit_prepare(const KernelArgs& ka, UState<C>& u, int level, int gl,
+                                             int unit, int (&Q2)[C], int (&Q1)[C]) {
     using Gr = Group<G, C>;
     const int rlo = max(u.lo, u.d - u.n);
     const int top = min(u.hi + 3, u.m);  // highest row the next three steps can reach
@@ -220,10 +258,43 @@ __device__ __forceinline__ void unit_prepare(const KernelArgs& ka, UState<C>& u,
                 u.bw |= typename Gr::Code(b_code(ka, u, int64_t(u.d) - 2 - (i0 + k))) << (2 * k);
             }
         }
-        if (ovf) {
-            u.active = false;
-            u.done = true;
-            u.overflow = true;
+        if (__any_sync(FULL, ovf)) {
+            // save the band for the next level (arrays are unshifted: sh = 0)
+            int32_t slot = -1;
+            if (ovf && gl == 0) slot = mig_alloc(ka, level);
+            slot = __shfl_sync(FULL, slot, unit * G);
+            if (ovf && slot >= 0) {
+                int32_t* rec = mig_record(ka, slot);
+#pragma unroll
+                for (int k = 0; k < C; ++k) {
+                    rec[kMigHeader + gl * C + k] = Q1[k];
+                    rec[kMigHeader + Gr::W + gl * C + k] = Q2[k];
+                }
+                if (gl == 0) {
+                    rec[MIG_KIND] = MIG_RELATIVE;
+                    rec[MIG_ROWS] = Gr::W;
+                    rec[MIG_D] = u.d;
+                    rec[MIG_BASE] = u.base;
+                    rec[MIG_LO] = u.lo;
+                    rec[MIG_HI] = u.hi;
+                    rec[MIG_BEST] = u.best;
+                    rec[MIG_T] = u.T;
+                    rec[MIG_T1] = u.T1;
+                    rec[MIG_T2] = u.T2;
+                    rec[MIG_BI] = u.bi;
+                    rec[MIG_BJ] = u.bj;
+                    rec[MIG_CELLS_LO] = int32_t(uint32_t(u.cells));
+                    rec[MIG_CELLS_HI] = int32_t(uint32_t(u.cells >> 32));
+                    rec[MIG_LEVEL] = level;
+                    ka.mig_slot[u.item] = slot;
+                }
+            }
+            if (ovf) {
+                u.active = false;
+                u.done = true;
+                u.overflow = true;
+                u.migrated = slot >= 0;
+            }
         }
     }
     // the next three steps read b' stream indices q .. q+2
@@ -366,6 +437,8 @@ __global__ void __launch_bounds__(128) k_group(KernelArgs ka, int level, int pla
     u.T = u.T1 = u.T2 = u.best = u.bi = u.bj = 0;
     u.X = 0;
     u.cells = 0ull;
+    u.cells0 = 0ull;
+    u.migrated = false;
     u.apos = u.bpos = 0;
     u.dir = 1;
     u.q0 = 0;
@@ -395,7 +468,7 @@ __global__ void __launch_bounds__(128) k_group(KernelArgs ka, int level, int pla
             }
         }
         if (!__any_sync(FULL, u.active)) break;
-        unit_prepare<G, C>(ka, u, gl, P0, P1);
+        unit_prepare<G, C>(ka, u, level, gl, unit, P0, P1);
         group_step<G, C>(ka, u, gl, unit, P0, P1, P2);
         group_step<G, C>(ka, u, gl, unit, P1, P2, P0);
         group_step<G, C>(ka, u, gl, unit, P2, P0, P1);

@@ -24,7 +24,7 @@ def ctx():
 def _reset(ctx):
     for opt, v in ((logan.OPT_FORCE_LEVEL, -1), (logan.OPT_MAX_LEVEL, logan.num_levels() - 1),
                    (logan.OPT_GRAPHS, 0), (logan.OPT_RING_CAP, 16), (logan.OPT_PLAIN_LEVEL, 1),
-                   (logan.OPT_TIMING, 0)):
+                   (logan.OPT_TIMING, 0), (logan.OPT_MIGRATION_MB, 64)):
         ctx.set_option(opt, v)
     yield
 
@@ -221,3 +221,18 @@ def test_escalation_policies(ctx):
     with pytest.raises(logan.LoganError):
         ctx.set_escalation([0] * n)
     ctx.set_escalation(default)
+
+
+@pytest.mark.parametrize("mig_mb", [0, 1, 64])
+def test_band_migration_budgets(ctx, mig_mb):
+    # unbounded X: every band grows to min(m, n) + 1 rows, so extensions climb
+    # through the levels; with 1 MiB the record pools run out and some
+    # extensions restart instead of resuming -- the results never change
+    b = synth.tiny_pairs(4000, 600, seed=41, X_choices=(200_000,))
+    ref = run_oracle(b)
+    ctx.set_option(logan.OPT_MIGRATION_MB, mig_mb)
+    try:
+        assert_same(run_gpu(ctx, b), ref, f"migration {mig_mb} MiB")
+        assert_same(run_gpu(ctx, b, plain=True), ref, f"plain, migration {mig_mb} MiB")
+    finally:
+        ctx.set_option(logan.OPT_MIGRATION_MB, 64)
