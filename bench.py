@@ -45,7 +45,13 @@ def parse():
     ap.add_argument("--steps", type=int, default=5)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
-    ap.add_argument("--pairs", type=int, default=100_000)
+    ap.add_argument("--pairs", type=int, default=None,
+                    help="pairs per GPU (default: the workload's own size)")
+    ap.add_argument("--workload", default="lognormal_batch",
+                    choices=["lognormal_batch", "uniform_pairs", "uneven_batch"],
+                    help="lognormal_batch (default, the headline configuration), "
+                         "uniform_pairs (1,000 x 2 kbp, X = 50) or uneven_batch "
+                         "(20,000 pairs of 1 kbp-1 Mbp, X per pair)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -63,20 +69,43 @@ def parse():
     return ap.parse_args()
 
 
-def workload(pairs: int, rank: int):
+DEFAULT_PAIRS = {"lognormal_batch": 100_000, "uniform_pairs": 1_000, "uneven_batch": 20_000}
+
+
+def workload(name: str, pairs: int, rank: int):
     from paper_2002_05200_gb300 import synth
-    b = synth.lognormal_batch(n_pairs=pairs, seed=2 + 1000 * rank)
-    b.meta["packed2bit"] = True
+    if name == "uniform_pairs":
+        b = synth.uniform_pairs(n_pairs=pairs, seed=0 + 1000 * rank)
+        b.meta["packed2bit"] = False  # the configuration feeds ASCII bases
+    elif name == "uneven_batch":
+        b = synth.uneven_batch(n_pairs=pairs, seed=3 + 1000 * rank)
+        b.meta["packed2bit"] = True
+    else:
+        b = synth.lognormal_batch(n_pairs=pairs, seed=2 + 1000 * rank)
+        b.meta["packed2bit"] = True
     return b
 
 
-def workload_config(b, pairs):
-    return {"workload": "lognormal_batch", "pairs": pairs, "median_len": 10_000,
+def workload_config(b, name, pairs):
+    packed_mb = (b.poolA.size + b.poolB.size) // 4 / 1e6
+    common = {"scoring": [1, -1, -1], "seed_len": 17,
+              "parallelism": "replicas (independent pairs per GPU, no collective)"}
+    if name == "uniform_pairs":
+        return {"workload": name, "pairs": pairs, "length": 2000, "error_rate": 0.15,
+                "X": 50, "input": "uint8 ASCII (packed on the GPU)",
+                "l2": "inputs smaller than L2 (4 MB): L2 flushed (512 MB write) between timed "
+                      "steps, outside the step's events",
+                **common}
+    if name == "uneven_batch":
+        return {"workload": name, "pairs": pairs,
+                "length_classes": "60/30/9/1 % in [1k,5k]/[5k,50k]/[50k,200k]/[200k,1M]",
+                "error_rate": "U[0.05, 0.20] per pair", "X": "per pair from {10,50,100,500}",
+                "input": "2-bit packed",
+                "l2": f"inputs larger than L2 (packed pools {packed_mb:.0f} MB), no flush", **common}
+    return {"workload": name, "pairs": pairs, "median_len": 10_000,
             "len_sigma": 0.5, "len_clip": [1000, 30000], "related_frac": 0.8,
-            "error_rate": 0.12, "seed_len": 17, "X": 100, "scoring": [1, -1, -1],
-            "input": "2-bit packed", "l2": "inputs larger than L2 (packed pools "
-            f"{(b.poolA.size + b.poolB.size) // 4 / 1e6:.0f} MB), no flush",
-            "parallelism": "replicas (independent pairs per GPU, no collective)"}
+            "error_rate": 0.12, "X": 100, "input": "2-bit packed",
+            "l2": f"inputs larger than L2 (packed pools {packed_mb:.0f} MB), no flush", **common}
 
 
 # ---------------------------------------------------------------- clocks
@@ -230,7 +259,7 @@ def cpu_sample(b, seconds: float, threads=None):
 def run_reference(args, rank, world):
     if rank != 0:
         return
-    b = workload(args.pairs, 0)
+    b = workload(args.workload, args.pairs, 0)
     per_step = max(1.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
         cpu_sample(b, per_step / 4)
@@ -246,7 +275,7 @@ def run_reference(args, rank, world):
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": workload_config(b, args.pairs),
+            "config": workload_config(b, args.workload, args.pairs),
             "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0,
@@ -257,6 +286,8 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------- GPU arm
 def main():
     args = parse()
+    if args.pairs is None:
+        args.pairs = DEFAULT_PAIRS[args.workload]
     rank = int(os.environ.get("RANK", "0"))
     world = int(os.environ.get("WORLD_SIZE", "1"))
     local = int(os.environ.get("LOCAL_RANK", "0"))
@@ -280,8 +311,9 @@ def main():
                 print(json.dumps({"serving": res}), flush=True)
         ctx0.close()
         return
-    b = workload(args.pairs, rank)
-    A, B, S, Xs = logan.batch_to_device(b, packed2bit=True, device=f"cuda:{local}")
+    b = workload(args.workload, args.pairs, rank)
+    packed = bool(b.meta["packed2bit"])
+    A, B, S, Xs = logan.batch_to_device(b, packed2bit=packed, device=f"cuda:{local}")
     ctx = logan.Context(local)
     stream = torch.cuda.Stream()
     ws = ctx.workspace(A, B, b.n_pairs)
@@ -296,19 +328,38 @@ def main():
         ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, workspace=ws, out=out,
                    stream=stream, plain=plain)
 
+    # inputs smaller than L2 (129 MB): flush L2 between timed steps by writing a
+    # 512 MB buffer, outside each step's own pair of events
+    small = (b.poolA.size + (0 if b.shared_pool else b.poolB.size)) // (4 if packed else 1) < (256 << 20)
+    flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}") if small else None
+
     def timed(fn, steps, warmup):
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 fn()
         barrier()
-        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        e0.record(stream)
-        for _ in range(steps):
-            fn()
-        e1.record(stream)
-        e1.synchronize()
-        barrier()
-        ms = e0.elapsed_time(e1)
+        if flush_buf is None:
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            for _ in range(steps):
+                fn()
+            e1.record(stream)
+            e1.synchronize()
+            barrier()
+            ms = e0.elapsed_time(e1)
+        else:
+            evs = []
+            for _ in range(steps):
+                with torch.cuda.stream(stream):
+                    flush_buf.fill_(1)
+                a, z = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+                a.record(stream)
+                fn()
+                z.record(stream)
+                evs.append((a, z))
+            torch.cuda.synchronize()
+            barrier()
+            ms = sum(a.elapsed_time(z) for a, z in evs)
         if world > 1:
             ms, _ = shard.reduce_step(ms, 0, device=f"cuda:{local}")
         return ms / steps
@@ -347,7 +398,8 @@ def main():
     line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
-            "dtype": "int32", "data": "synthetic", "config": workload_config(b, args.pairs),
+            "dtype": "int32", "data": "synthetic",
+            "config": workload_config(b, args.workload, args.pairs),
             "clocks": clocks, "gpu_launches": launches * args.steps,
             "cells_per_step": tot_cells,
             "levels": {"ms": [round(float(v), 4) for v in level_ms],
@@ -385,9 +437,9 @@ def main():
         hX = Xs.cpu().pin_memory() if Xs is not None else None
         hout = torch.empty_like(out, device="cpu").pin_memory()
         dA = logan.DevicePool(torch.empty_like(A.bases), torch.empty_like(A.offsets),
-                              torch.empty_like(A.lengths), True, A.pool_bases)
+                              torch.empty_like(A.lengths), packed, A.pool_bases)
         dB = logan.DevicePool(torch.empty_like(B.bases), torch.empty_like(B.offsets),
-                              torch.empty_like(B.lengths), True, B.pool_bases)
+                              torch.empty_like(B.lengths), packed, B.pool_bases)
         dS = torch.empty_like(S)
         h2d = sum(t.numel() * t.element_size() for t in list(hA.values()) + list(hB.values()) + [hS])
         d2h = hout.numel() * hout.element_size()
@@ -411,7 +463,7 @@ def main():
                        "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                        "ms_per_step": ms_e2e, "results_identical": ok}
 
-    if not args.no_serving:
+    if not args.no_serving and args.workload == "lognormal_batch":
         line["serving"] = serving_run(ctx, args.serving_rate, args.serving_requests,
                                       args.serving_budget_gb, args.serving_inflight)
         line["metric_serving"] = {"p50_ms": line["serving"]["p50_ms"],

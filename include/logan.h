@@ -136,8 +136,9 @@ int logan_workspace_size(const logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   workspace: device buffer of >= logan_workspace_size bytes, 256-aligned.
  *   out: device logan_result_t[n_pairs].
  * Pipeline on `stream`: pack (ASCII input only) -> split + seed score ->
- * length/X binning -> persistent extension kernels (one per band-width
- * class, widest last, longest items first) -> combine. With graphs enabled
+ * length/X binning -> phase 1: one persistent extension kernel per window
+ * level over its binned items, longest first, all levels concurrently ->
+ * phase 2: the escalated items, narrowest level first -> combine. With graphs enabled
  * (logan_set_option) the launch sequence is captured once per shape and
  * replayed. Returns LOGAN_EINVAL for invalid scalars or pointers,
  * LOGAN_ENOMEM if ws_bytes is too small, LOGAN_ECUDA on a launch failure.
@@ -170,8 +171,9 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  * memory is one static device array of LOGAN_NOALLOC_SCRATCH_BYTES that
  * every GPU loading the library holds until the process exits.
  *   - No cudaMalloc/cudaFree or other allocating call, and no CUDA graph is
- *     built (the context's graph option is ignored for this call), and no
- *     band-state records are kept (LOGAN_OPT_MIGRATION_MB is 0 for the call).
+ *     built (the context's graph option is ignored for this call), no
+ *     band-state records are kept (LOGAN_OPT_MIGRATION_MB is 0 for the call)
+ *     and all levels run on `stream` (LOGAN_OPT_CONCURRENT is 0).
  *   - The fallback window for very wide bands is LOGAN_NOALLOC_RING_ROWS
  *     rows (wider bands give LOGAN_ERANGE for that pair).
  *   - A batch whose scratch need (logan_workspace_size with that window)
@@ -207,6 +209,7 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   LOGAN_OPT_PLAIN_LEVEL   window level of the plain form (default 1)
  *   LOGAN_OPT_DEVICE        (read-only) the context's device
  *   LOGAN_OPT_MIGRATION_MB  band-state migration budget (below)
+ *   LOGAN_OPT_CONCURRENT    concurrent start levels (below)
  */
 #define LOGAN_OPT_GRAPHS 1
 #define LOGAN_OPT_TIMING 2
@@ -219,6 +222,10 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                                     (default 64; 0: an overflowing extension
                                     restarts at the next level instead of
                                     resuming); changes the workspace size */
+#define LOGAN_OPT_CONCURRENT 9   /* 1 (default): the binned items of every
+                                    window level run concurrently, on streams
+                                    the context creates once per caller stream;
+                                    0: level after level on the caller stream */
 int logan_set_option(logan_ctx_t *ctx, int option, int64_t value);
 int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
 
@@ -230,7 +237,10 @@ int logan_level_info(int level, int *window_cells, int *threads_per_unit);
  * call records CUDA events around every extension level on its stream; this
  * function synchronises on them and reads the level counters from the
  * workspace, which must not have been reused since).
- *   level_ms[k]  device time of window level k (k < logan_num_levels()),
+ *   level_ms[k]  device time of window level k (k < logan_num_levels()):
+ *                its phase-1 launch plus its phase-2 launch; with
+ *                LOGAN_OPT_CONCURRENT the phase-1 launches overlap, so the
+ *                levels' times can add up to more than total_ms;
  *                level_ms[logan_num_levels()] = the global-memory fallback;
  *   total_ms     the whole pipeline of the call;
  *   items[k]     extensions that ran at level k (started there or escalated
@@ -311,16 +321,22 @@ int logan_autotune_save(const logan_ctx_t *ctx, const char *path);
  * copy-out on the slot's stream and returns the bytes when the stream
  * reaches the request's end.  Requests on different slots overlap on the GPU;
  * each has its own workspace, so its results are the same alone and in any
- * mix.  The server uses the context exclusively (graphs and timing off)
- * until logan_server_destroy; do not call other functions on that context
- * meanwhile.
+ * mix.  The server also owns a pinned host staging arena (budget_bytes / 8,
+ * clamped to [16 MiB, 1 GiB]): the scheduler copies a request's inputs into
+ * it, the results come back into it and are copied to the caller's buffer
+ * when the request completes, so no copy ever waits for another request's
+ * kernels.  Admission needs room in both arenas.  A request whose inputs and
+ * results exceed the whole staging arena is copied directly from and to the
+ * caller's buffers (correct; with pageable buffers the scheduler thread then
+ * waits for that request's copies).  The server uses the context
+ * exclusively (graphs and timing off) until logan_server_destroy; do not call
+ * other functions on that context meanwhile.
  */
 typedef struct logan_server logan_server_t;
 
 /* One request.  Every pointer is HOST memory owned by the caller and must
- * stay valid until the request is done (pinned memory lets the copies
- * overlap with the GPU; pageable memory works but blocks the scheduler
- * thread during its copies).  A.bases/B.bases: ASCII bytes (pool_bases of
+ * stay valid until the request is done (pageable or pinned: the server
+ * stages them).  A.bases/B.bases: ASCII bytes (pool_bases of
  * them) or 2-bit words (ceil(pool_bases/16) of them).  same_pool != 0: B is
  * A.  results: n_pairs logan_result_t written by the server. */
 typedef struct {

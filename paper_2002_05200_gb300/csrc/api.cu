@@ -20,7 +20,20 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kEvSets = 32;        // timed calls whose events are kept
-constexpr int kEvPerSet = kNumLevels + 4;
+// per timed call: phase-1 start/end and phase-2 start/end of every level,
+// then pipeline start, fallback start, fallback end, pipeline end
+constexpr int EV_P1S = 0, EV_P1E = kNumLevels, EV_P2S = 2 * kNumLevels, EV_P2E = 3 * kNumLevels;
+constexpr int EV_START = 4 * kNumLevels, EV_RING_S = EV_START + 1, EV_RING_E = EV_START + 2,
+              EV_END = EV_START + 3;
+constexpr int kEvPerSet = 4 * kNumLevels + 4;
+
+// Streams on which the start levels of one caller stream run concurrently.
+struct AuxSet {
+    cudaStream_t main = nullptr;
+    cudaStream_t st[kNumLevels] = {};
+    cudaEvent_t fork = nullptr;
+    cudaEvent_t join[kNumLevels] = {};
+};
 inline size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
 struct GraphEntry {
@@ -52,8 +65,12 @@ struct logan_ctx {
         int first_level = 0;
         int max_level = 0;
         uint32_t launches = 0;
+        uint32_t p1_levels = 0;  // bit l: phase-1 events of level l recorded
+        uint32_t p2_levels = 0;
         Counters* counters = nullptr;
     } calls[kEvSets];
+    int64_t concurrent = 1;  // run the start levels of a batch concurrently
+    std::vector<AuxSet> aux;
     bool timing_pending = false;
     uint32_t launches_last = 0;
     // graph cache
@@ -150,12 +167,35 @@ void default_table(LevelTable& t) {
     t.only_xclass = -1;
 }
 
-int launch_level(logan_ctx* c, int level, const KernelArgs& ka, cudaStream_t s) {
+int launch_level(logan_ctx* c, int level, const KernelArgs& ka, int phase, cudaStream_t s) {
     const int per_sm = std::max(1, c->blocks_per_sm[level]);
     const int grid = c->num_sms * per_sm;
-    cudaError_t e = level < kWarpLevels ? launch_warp_level_persistent(level, ka, grid, s)
-                                        : launch_cta_level(level, ka, grid, 0, s);
+    cudaError_t e = level < kWarpLevels ? launch_warp_level_persistent(level, ka, grid, phase, s)
+                                        : launch_cta_level(level, ka, grid, phase, s);
     return e == cudaSuccess ? LOGAN_OK : LOGAN_ECUDA;
+}
+
+// The auxiliary streams of caller stream `s` (created on first use).
+AuxSet* aux_for(logan_ctx* c, cudaStream_t s) {
+    for (auto& a : c->aux)
+        if (a.main == s) return &a;
+    AuxSet a;
+    a.main = s;
+    bool ok = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess;
+    for (int l = 0; ok && l < kNumLevels; ++l) {
+        ok = cudaStreamCreateWithFlags(&a.st[l], cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&a.join[l], cudaEventDisableTiming) == cudaSuccess;
+    }
+    if (!ok) {
+        for (int l = 0; l < kNumLevels; ++l) {
+            if (a.st[l]) cudaStreamDestroy(a.st[l]);
+            if (a.join[l]) cudaEventDestroy(a.join[l]);
+        }
+        if (a.fork) cudaEventDestroy(a.fork);
+        return nullptr;
+    }
+    c->aux.push_back(a);
+    return &c->aux.back();
 }
 
 // The whole pipeline on `s` (no synchronisation).  plain != 0: one-launch
@@ -177,7 +217,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     }
     cudaError_t e = cudaSuccess;
     uint32_t launches = 0;
-    if (timing) e = cudaEventRecord(c->ev[kNumLevels + 1], s);
+    if (timing) e = cudaEventRecord(c->ev[EV_START], s);
     if (e == cudaSuccess && !A->packed2bit && A->pool_bases) {
         e = launch_pack(pa, reinterpret_cast<uint32_t*>(ws + L.wordsA), s);
         ++launches;
@@ -240,32 +280,63 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         ka.mig_pool[l] = L.mig_cap[l] ? reinterpret_cast<int32_t*>(ws + L.mig_pool[l]) : nullptr;
     }
     ka.mig_slot = reinterpret_cast<int32_t*>(ws + L.mig_slot);
-    for (int lvl = plain ? first : 0; lvl <= maxl; ++lvl) {
-        if (timing && cudaEventRecord(c->ev[lvl], s) != cudaSuccess) return LOGAN_ECUDA;
-        int rc = LOGAN_OK;
-        if (plain && lvl == first) {
-            e = lvl < kWarpLevels ? launch_warp_level_plain(lvl, ka, s)
-                                  : launch_cta_level(lvl, ka, c->num_sms * std::max(1, c->blocks_per_sm[lvl]), 1, s);
-            rc = e == cudaSuccess ? LOGAN_OK : LOGAN_ECUDA;
-        } else {
-            rc = launch_level(c, lvl, ka, s);
+    uint32_t p1_levels = 0, p2_levels = 0;
+    cudaEvent_t* ev = c->ev;
+    auto rec = [&](int idx, cudaStream_t st) {
+        return !timing || cudaEventRecord(ev[idx], st) == cudaSuccess;
+    };
+    if (plain) {
+        // phase 1: the one-launch form at `first`, in input order
+        if (!rec(EV_P1S + first, s)) return LOGAN_ECUDA;
+        e = first < kWarpLevels
+                ? launch_warp_level_plain(first, ka, s)
+                : launch_cta_level(first, ka, c->num_sms * std::max(1, c->blocks_per_sm[first]),
+                                   PHASE_PLAIN, s);
+        if (e != cudaSuccess || !rec(EV_P1E + first, s)) return LOGAN_ECUDA;
+        p1_levels |= 1u << first;
+        ++launches;
+    } else {
+        // phase 1: every level's binned items; the levels share no queue entry,
+        // so they run concurrently on their own streams
+        AuxSet* ax = c->concurrent ? aux_for(c, s) : nullptr;
+        if (ax && cudaEventRecord(ax->fork, s) != cudaSuccess) return LOGAN_ECUDA;
+        for (int lvl = 0; lvl <= maxl; ++lvl) {
+            cudaStream_t st = ax ? ax->st[lvl] : s;
+            if (ax && cudaStreamWaitEvent(st, ax->fork, 0) != cudaSuccess) return LOGAN_ECUDA;
+            if (!rec(EV_P1S + lvl, st)) return LOGAN_ECUDA;
+            if (launch_level(c, lvl, ka, PHASE_INITIAL, st) != LOGAN_OK) return LOGAN_ECUDA;
+            if (!rec(EV_P1E + lvl, st)) return LOGAN_ECUDA;
+            if (ax && (cudaEventRecord(ax->join[lvl], st) != cudaSuccess ||
+                       cudaStreamWaitEvent(s, ax->join[lvl], 0) != cudaSuccess))
+                return LOGAN_ECUDA;
+            p1_levels |= 1u << lvl;
+            ++launches;
         }
-        if (rc) return rc;
+    }
+    // phase 2: escalated items, narrowest level first (each level can only
+    // receive items from narrower ones)
+    for (int lvl = (plain ? first + 1 : 0); lvl <= maxl; ++lvl) {
+        if (!rec(EV_P2S + lvl, s)) return LOGAN_ECUDA;
+        if (launch_level(c, lvl, ka, PHASE_ESCALATED, s) != LOGAN_OK) return LOGAN_ECUDA;
+        if (!rec(EV_P2E + lvl, s)) return LOGAN_ECUDA;
+        p2_levels |= 1u << lvl;
         ++launches;
     }
     // ring fallback: one resident block per ring slot
-    if (timing && cudaEventRecord(c->ev[kNumLevels], s) != cudaSuccess) return LOGAN_ECUDA;
+    if (!rec(EV_RING_S, s)) return LOGAN_ECUDA;
     if (launch_ring(ka, int(L.ring_slots), s) != cudaSuccess) return LOGAN_ECUDA;
-    if (timing && cudaEventRecord(c->ev[kNumLevels + 2], s) != cudaSuccess) return LOGAN_ECUDA;
+    if (!rec(EV_RING_E, s)) return LOGAN_ECUDA;
     if (launch_combine(seeds, info, ext, n_pairs, out, s) != cudaSuccess) return LOGAN_ECUDA;
     launches += 2;  // ring + combine
     c->launches_last = launches;
     if (timing) {
-        if (cudaEventRecord(c->ev[kNumLevels + 3], s) != cudaSuccess) return LOGAN_ECUDA;
+        if (!rec(EV_END, s)) return LOGAN_ECUDA;
         auto& ci = c->calls[c->timed_calls % kEvSets];
         ci.first_level = plain ? first : 0;
         ci.max_level = maxl;
         ci.launches = launches;
+        ci.p1_levels = p1_levels;
+        ci.p2_levels = p2_levels;
         ci.counters = counters;
         c->timed_calls += 1;
         c->timing_pending = true;
@@ -299,7 +370,8 @@ int extend_common(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         uint64_t(uint32_t(gap)), uint64_t(uint32_t(X)), uint64_t(uintptr_t(Xs)),
         uint64_t(uintptr_t(seeds)), uint64_t(uintptr_t(out)), uint64_t(uintptr_t(ws)),
         uint64_t(uintptr_t(stream)), uint64_t(c->force_level), uint64_t(c->max_level),
-        uint64_t(c->ring_log2), uint64_t(c->plain_level), uint64_t(c->mig_mb)};
+        uint64_t(c->ring_log2), uint64_t(c->plain_level), uint64_t(c->mig_mb),
+        uint64_t(c->concurrent)};
     for (const logan_seqs_t* p : {A, B}) {
         key.push_back(uint64_t(uintptr_t(p->bases)));
         key.push_back(uint64_t(uintptr_t(p->offsets)));
@@ -313,6 +385,8 @@ int extend_common(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     for (auto& ge : c->graphs)
         if (ge.key == key) hit = &ge;
     if (!hit) {
+        // the auxiliary streams are created outside the capture
+        if (c->concurrent && !plain && !aux_for(c, s)) return LOGAN_ECUDA;
         cudaGraph_t graph = nullptr;
         if (cudaStreamBeginCapture(s, cudaStreamCaptureModeThreadLocal) != cudaSuccess)
             return LOGAN_ECUDA;
@@ -441,6 +515,16 @@ void logan_ctx_destroy(logan_ctx_t* c) {
     DeviceGuard g(c->device);
     for (auto& ge : c->graphs)
         if (ge.exec) cudaGraphExecDestroy(ge.exec);
+    for (auto& a : c->aux) {
+        for (int l = 0; l < kNumLevels; ++l) {
+            if (a.st[l]) {
+                cudaStreamSynchronize(a.st[l]);
+                cudaStreamDestroy(a.st[l]);
+            }
+            if (a.join[l]) cudaEventDestroy(a.join[l]);
+        }
+        if (a.fork) cudaEventDestroy(a.fork);
+    }
     for (auto& set : c->evs)
         for (auto& ev : set)
             if (ev) cudaEventDestroy(ev);
@@ -495,6 +579,7 @@ int logan_set_option(logan_ctx_t* c, int option, int64_t v) {
             if (v < 0 || v > 4096) return LOGAN_EINVAL;
             c->mig_mb = v;
             return LOGAN_OK;
+        case LOGAN_OPT_CONCURRENT: c->concurrent = v ? 1 : 0; return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }
@@ -510,6 +595,7 @@ int logan_get_option(const logan_ctx_t* c, int option, int64_t* v) {
         case LOGAN_OPT_PLAIN_LEVEL: *v = c->plain_level; return LOGAN_OK;
         case LOGAN_OPT_DEVICE: *v = c->device; return LOGAN_OK;
         case LOGAN_OPT_MIGRATION_MB: *v = c->mig_mb; return LOGAN_OK;
+        case LOGAN_OPT_CONCURRENT: *v = c->concurrent; return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }
@@ -531,18 +617,24 @@ int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
     const uint64_t call = c->timed_calls - 1 - uint64_t(back);
     cudaEvent_t* ev = c->evs[call % kEvSets];
     const auto& ci = c->calls[call % kEvSets];
-    if (cudaEventSynchronize(ev[kNumLevels + 3]) != cudaSuccess) return LOGAN_ECUDA;
+    if (cudaEventSynchronize(ev[EV_END]) != cudaSuccess) return LOGAN_ECUDA;
     std::memset(st, 0, sizeof(*st));
-    for (int l = ci.first_level; l <= ci.max_level; ++l) {
-        // level l runs from ev[l] to the next recorded event
-        const int nxt = l + 1 <= ci.max_level ? l + 1 : kNumLevels;
-        if (cudaEventElapsedTime(&st->level_ms[l], ev[l], ev[nxt]) != cudaSuccess)
-            return LOGAN_ECUDA;
+    for (int l = 0; l < kNumLevels; ++l) {
+        float ms = 0.f;
+        if ((ci.p1_levels >> l) & 1u) {
+            if (cudaEventElapsedTime(&ms, ev[EV_P1S + l], ev[EV_P1E + l]) != cudaSuccess)
+                return LOGAN_ECUDA;
+            st->level_ms[l] += ms;
+        }
+        if ((ci.p2_levels >> l) & 1u) {
+            if (cudaEventElapsedTime(&ms, ev[EV_P2S + l], ev[EV_P2E + l]) != cudaSuccess)
+                return LOGAN_ECUDA;
+            st->level_ms[l] += ms;
+        }
     }
-    if (cudaEventElapsedTime(&st->level_ms[kNumLevels], ev[kNumLevels], ev[kNumLevels + 2]) !=
-        cudaSuccess)
+    if (cudaEventElapsedTime(&st->level_ms[kNumLevels], ev[EV_RING_S], ev[EV_RING_E]) != cudaSuccess)
         return LOGAN_ECUDA;
-    if (cudaEventElapsedTime(&st->total_ms, ev[kNumLevels + 1], ev[kNumLevels + 3]) != cudaSuccess)
+    if (cudaEventElapsedTime(&st->total_ms, ev[EV_START], ev[EV_END]) != cudaSuccess)
         return LOGAN_ECUDA;
     if (back == 0) {
         // the level counters live in the workspace: valid for the last call only

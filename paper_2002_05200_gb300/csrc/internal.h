@@ -52,10 +52,11 @@ __device__ __forceinline__ int escalate(const KernelArgs& ka, int level) {
 }
 
 // extension kernels (xdrop_group.cu / xdrop_cta.cu / xdrop_ring.cu)
-cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid, cudaStream_t s);
+cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid, int phase,
+                                         cudaStream_t s);
 cudaError_t launch_warp_level_plain(int level, const KernelArgs& ka, cudaStream_t s);
 int warp_level_blocks_per_sm(int level);
-cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int plain, cudaStream_t s);
+cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int phase, cudaStream_t s);
 int cta_level_blocks_per_sm(int level);
 cudaError_t launch_ring(const KernelArgs& ka, int grid, cudaStream_t s);
 

@@ -88,7 +88,25 @@ struct Counters {
     unsigned int pad;
     unsigned long long cells[kNumLevels + 1];  // cells computed by each level
     unsigned int mig_used[kNumLevels];         // migration records written per level
+    unsigned int head2[kNumLevels + 1];        // pop cursor of the escalated entries
 };
+
+// Which entries of a level's queue a launch processes: the binned (initial)
+// entries [0, started) in phase 1, the escalated ones [started, tail) in
+// phase 2; the plain form takes item i directly.
+constexpr int PHASE_INITIAL = 0;
+constexpr int PHASE_ESCALATED = 1;
+constexpr int PHASE_PLAIN = 2;
+
+// Next queue slot of `level` for this phase, or ~0u when the range is used up.
+__device__ __forceinline__ unsigned int pop_slot(Counters* c, int level, int phase) {
+    if (phase == PHASE_INITIAL) {
+        const unsigned int s = atomicAdd(&c->head[level], 1u);
+        return s < c->started[level] ? s : ~0u;
+    }
+    const unsigned int s = c->started[level] + atomicAdd(&c->head2[level], 1u);
+    return s < c->tail[level] ? s : ~0u;
+}
 
 // Band-state migration.  A unit whose band outgrows its window writes its
 // last two anti-diagonals (rows [base, base + rows)) and its scalars to a

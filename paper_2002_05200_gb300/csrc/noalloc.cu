@@ -58,22 +58,26 @@ extern "C" int logan_extend_batch_noalloc(logan_ctx_t* ctx, const logan_seqs_t* 
                                           int32_t gap, int32_t X, const int32_t* X_per_pair,
                                           logan_result_t* out, void* stream) {
     if (!ctx) return LOGAN_EINVAL;
-    int64_t device = -1, ring = 0, graphs = 0, mig = 0;
+    int64_t device = -1, ring = 0, graphs = 0, mig = 0, conc = 0;
     if (logan_get_option(ctx, LOGAN_OPT_DEVICE, &device) != LOGAN_OK ||
         logan_get_option(ctx, LOGAN_OPT_RING_CAP, &ring) != LOGAN_OK ||
         logan_get_option(ctx, LOGAN_OPT_GRAPHS, &graphs) != LOGAN_OK ||
-        logan_get_option(ctx, LOGAN_OPT_MIGRATION_MB, &mig) != LOGAN_OK)
+        logan_get_option(ctx, LOGAN_OPT_MIGRATION_MB, &mig) != LOGAN_OK ||
+        logan_get_option(ctx, LOGAN_OPT_CONCURRENT, &conc) != LOGAN_OK)
         return LOGAN_EINVAL;
     void* scratch = nullptr;
     int rc = scratch_address(int(device), &scratch);
     if (rc != LOGAN_OK) return rc;
     // this form always uses the smaller fallback window, keeps no band-state
-    // records (a band that outgrows its window restarts at the next level)
-    // and never builds a CUDA graph (instantiating one allocates); the
-    // caller's settings are restored afterwards
+    // records (a band that outgrows its window restarts at the next level),
+    // runs all levels on the caller's stream and never builds a CUDA graph
+    // (instantiating one allocates); the caller's settings are restored
+    // afterwards
     rc = logan_set_option(ctx, LOGAN_OPT_RING_CAP, LOGAN_NOALLOC_RING_LOG2);
     if (rc == LOGAN_OK) rc = logan_set_option(ctx, LOGAN_OPT_GRAPHS, 0);
     if (rc == LOGAN_OK) rc = logan_set_option(ctx, LOGAN_OPT_MIGRATION_MB, 0);
+    // runs every level on the caller's stream (no auxiliary streams to create)
+    if (rc == LOGAN_OK) rc = logan_set_option(ctx, LOGAN_OPT_CONCURRENT, 0);
     size_t need = 0;
     if (rc == LOGAN_OK) rc = logan_workspace_size(ctx, seqsA, seqsB, n_pairs, &need);
     if (rc == LOGAN_OK && need > size_t(LOGAN_NOALLOC_SCRATCH_BYTES)) rc = LOGAN_ENOMEM;
@@ -84,5 +88,6 @@ extern "C" int logan_extend_batch_noalloc(logan_ctx_t* ctx, const logan_seqs_t* 
     logan_set_option(ctx, LOGAN_OPT_RING_CAP, ring);
     logan_set_option(ctx, LOGAN_OPT_GRAPHS, graphs);
     logan_set_option(ctx, LOGAN_OPT_MIGRATION_MB, mig);
+    logan_set_option(ctx, LOGAN_OPT_CONCURRENT, conc);
     return rc;
 }

@@ -183,6 +183,7 @@ __global__ void k_bin_scan(uint32_t* __restrict__ hist, Counters* __restrict__ c
     }
     if (t <= kNumLevels) {
         c->head[t] = 0u;
+        c->head2[t] = 0u;
         c->cells[t] = 0ull;
     }
     if (t < kNumLevels) c->mig_used[t] = 0u;
@@ -209,10 +210,13 @@ __global__ void k_reset_counters(Counters* c, uint32_t first_items, int first_le
     const int t = threadIdx.x;
     if (t <= kNumLevels) {
         c->head[t] = 0u;
+        c->head2[t] = 0u;
         c->tail[t] = 0u;
-        c->started[t] = (t == first_level) ? first_items : 0u;
+        c->started[t] = 0u;  // the plain kernel takes items directly
         c->cells[t] = 0ull;
     }
+    (void)first_items;
+    (void)first_level;
     if (t < kNumLevels) c->mig_used[t] = 0u;
 }
 

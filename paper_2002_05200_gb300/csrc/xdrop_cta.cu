@@ -303,16 +303,23 @@ __device__ bool cta_extend(const KernelArgs& ka, uint32_t id, int level, const E
 }
 
 template <int C, int NW>
-__global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int level, int plain) {
+__global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int level, int phase) {
     __shared__ CtaSmem<C, NW> sm;
-    const unsigned int count = plain ? ka.n_items : ka.counters->tail[level];
+    const bool plain = phase == PHASE_PLAIN;
     const uint32_t* q = ka.queues + size_t(level) * ka.qcap;
     for (;;) {
-        if (threadIdx.x == 0) sm.slot = atomicAdd(&ka.counters->head[level], 1u);
+        if (threadIdx.x == 0) {
+            if (plain) {
+                const unsigned int s = atomicAdd(&ka.counters->head[level], 1u);
+                sm.slot = s < ka.n_items ? s : ~0u;
+            } else {
+                sm.slot = pop_slot(ka.counters, level, phase);
+            }
+        }
         __syncthreads();
         const unsigned int slot = sm.slot;
         __syncthreads();
-        if (slot >= count) break;
+        if (slot == ~0u) break;
         const uint32_t id = plain ? slot : q[slot];
         const Item it = ka.items[id];
         if (it.flags & ITEM_SKIP) continue;
@@ -348,11 +355,11 @@ __global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int l
 
 }  // namespace
 
-cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int plain,
+cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int phase,
                              cudaStream_t s) {
     switch (level) {
-        case 6: k_cta_persistent<16, 4><<<grid, 128, 0, s>>>(ka, level, plain); break;
-        case 7: k_cta_persistent<8, 16><<<grid, 512, 0, s>>>(ka, level, plain); break;
+        case 6: k_cta_persistent<16, 4><<<grid, 128, 0, s>>>(ka, level, phase); break;
+        case 7: k_cta_persistent<8, 16><<<grid, 512, 0, s>>>(ka, level, phase); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

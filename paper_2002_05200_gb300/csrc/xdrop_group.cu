@@ -408,12 +408,12 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
 }
 
 template <int G, int C>
-__global__ void __launch_bounds__(128) k_group(KernelArgs ka, int level, int plain) {
+__global__ void __launch_bounds__(128) k_group(KernelArgs ka, int level, int phase) {
     using Gr = Group<G, C>;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G, unit = lane / G;
     const unsigned int umask = (G == 32) ? FULL : (((1u << G) - 1u) << (unit * G));
-    const unsigned int count = plain ? ka.n_items : ka.counters->tail[level];
+    const bool plain = phase == PHASE_PLAIN;
     const uint32_t* q = ka.queues + size_t(level) * ka.qcap;
     // plain form: one fixed item per unit, in input order
     const uint32_t plain_id =
@@ -454,14 +454,14 @@ __global__ void __launch_bounds__(128) k_group(KernelArgs ka, int level, int pla
                 // this unit takes its next item (lanes of the unit only)
                 uint32_t id = 0xffffffffu;
                 if (plain) {
-                    if (fresh && plain_id < count && !(ka.items[plain_id].flags & ITEM_SKIP))
+                    if (fresh && plain_id < ka.n_items && !(ka.items[plain_id].flags & ITEM_SKIP))
                         id = plain_id;
                     fresh = false;
                 } else {
                     unsigned int slot = 0u;
-                    if (gl == 0) slot = atomicAdd(&ka.counters->head[level], 1u);
+                    if (gl == 0) slot = pop_slot(ka.counters, level, phase);
                     slot = __shfl_sync(umask, slot, unit * G);
-                    if (slot < count) id = q[slot];
+                    if (slot != ~0u) id = q[slot];
                 }
                 if (id != 0xffffffffu) unit_init<G, C>(ka, u, id, gl, P0, P1);
                 else exhausted = true;
@@ -482,10 +482,10 @@ __global__ void __launch_bounds__(128) k_group(KernelArgs ka, int level, int pla
 #define LOGAN_GROUP_LEVELS(X) \
     X(0, 8, 4) X(1, 8, 8) X(2, 8, 16) X(3, 16, 16) X(4, 32, 16) X(5, 32, 32)
 
-cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid,
+cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid, int phase,
                                          cudaStream_t s) {
     switch (level) {
-#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, 0); break;
+#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, phase); break;
         LOGAN_GROUP_LEVELS(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
@@ -504,7 +504,7 @@ cudaError_t launch_warp_level_plain(int level, const KernelArgs& ka, cudaStream_
     const unsigned int grid = (ka.n_items + units_per_block - 1) / units_per_block;
     if (grid == 0) return cudaSuccess;
     switch (level) {
-#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, 1); break;
+#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, PHASE_PLAIN); break;
         LOGAN_GROUP_LEVELS(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;

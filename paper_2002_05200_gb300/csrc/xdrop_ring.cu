@@ -113,14 +113,13 @@ __global__ void __launch_bounds__(kRingThreads) k_ring(KernelArgs ka) {
     __shared__ Red sh[kRingWarps];
     __shared__ unsigned int s_slot;
     int32_t* R = ka.ring + size_t(blockIdx.x) * 3u * ka.ring_cap;
-    const unsigned int count = ka.counters->tail[kNumLevels];
     const uint32_t* q = ka.queues + size_t(kNumLevels) * ka.qcap;
     for (;;) {
-        if (threadIdx.x == 0) s_slot = atomicAdd(&ka.counters->head[kNumLevels], 1u);
+        if (threadIdx.x == 0) s_slot = pop_slot(ka.counters, kNumLevels, PHASE_ESCALATED);
         __syncthreads();
         const unsigned int slot = s_slot;
         __syncthreads();
-        if (slot >= count) break;
+        if (slot == ~0u) break;
         const uint32_t id = q[slot];
         const Item it = ka.items[id];
         ExtRes r;

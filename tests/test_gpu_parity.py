@@ -24,7 +24,8 @@ def ctx():
 def _reset(ctx):
     for opt, v in ((logan.OPT_FORCE_LEVEL, -1), (logan.OPT_MAX_LEVEL, logan.num_levels() - 1),
                    (logan.OPT_GRAPHS, 0), (logan.OPT_RING_CAP, 16), (logan.OPT_PLAIN_LEVEL, 1),
-                   (logan.OPT_TIMING, 0), (logan.OPT_MIGRATION_MB, 64)):
+                   (logan.OPT_TIMING, 0), (logan.OPT_MIGRATION_MB, 64),
+                   (logan.OPT_CONCURRENT, 1)):
         ctx.set_option(opt, v)
     yield
 
@@ -236,3 +237,22 @@ def test_band_migration_budgets(ctx, mig_mb):
         assert_same(run_gpu(ctx, b, plain=True), ref, f"plain, migration {mig_mb} MiB")
     finally:
         ctx.set_option(logan.OPT_MIGRATION_MB, 64)
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_concurrent_and_serial_levels_agree(ctx, graphs):
+    # start levels on their own streams (default) or level after level on
+    # the caller's stream: same results, also when captured into a graph
+    import torch
+    b = synth.uneven_batch(n_pairs=400, max_len=20_000, seed=53)
+    ref = run_oracle(b)
+    stream = torch.cuda.Stream()
+    for conc in (1, 0):
+        ctx.set_option(logan.OPT_CONCURRENT, conc)
+        assert ctx.get_option(logan.OPT_CONCURRENT) == conc
+        with torch.cuda.stream(stream):
+            A, B, S, Xs = logan.batch_to_device(b, packed2bit=True)
+            ctx.set_option(logan.OPT_GRAPHS, 1 if graphs else 0)
+            out = ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, stream=stream)
+        stream.synchronize()
+        assert_same(logan.results_to_numpy(out), ref, f"concurrent={conc} graphs={graphs}")
