@@ -31,6 +31,10 @@ import time
 
 import numpy as np
 
+# one hardware work queue per serving slot (the default is 8; must be set
+# before CUDA initialises)
+os.environ.setdefault("CUDA_DEVICE_MAX_CONNECTIONS", "32")
+
 ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
@@ -60,10 +64,10 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the timed persistent steps (for profiler runs)")
     ap.add_argument("--no-serving", action="store_true")
-    ap.add_argument("--serving-rate", type=float, default=60.0, help="requests per second")
+    ap.add_argument("--serving-rate", type=float, default=80.0, help="requests per second")
     ap.add_argument("--serving-requests", type=int, default=240)
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
-    ap.add_argument("--serving-inflight", type=int, default=8)
+    ap.add_argument("--serving-inflight", type=int, default=32)
     ap.add_argument("--serving-sweep", type=str, default="",
                     help="comma-separated rates: print one serving JSON line per rate and exit")
     return ap.parse_args()

@@ -328,9 +328,14 @@ int logan_autotune_save(const logan_ctx_t *ctx, const char *path);
  * kernels.  Admission needs room in both arenas.  A request whose inputs and
  * results exceed the whole staging arena is copied directly from and to the
  * caller's buffers (correct; with pageable buffers the scheduler thread then
- * waits for that request's copies).  The server uses the context
- * exclusively (graphs and timing off) until logan_server_destroy; do not call
- * other functions on that context meanwhile.
+ * waits for that request's copies); so is a request whose host buffers are
+ * all pinned.  The server uses the context exclusively (graphs, timing and
+ * concurrent levels off: each request runs on its slot's stream) until
+ * logan_server_destroy, which restores those three options; do not call other functions on that context
+ * meanwhile.  The slots overlap only as far as the device's hardware work
+ * queues allow: set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) to at least
+ * max_inflight before the process initialises CUDA, or a long extension in
+ * one slot can delay launches of the slots that share its queue.
  */
 typedef struct logan_server logan_server_t;
 

@@ -14,9 +14,21 @@
 // drain, and results do not depend on what else is in flight (each request
 // has its own workspace).  The paper retrieves results asynchronously as
 // kernels complete (Sec. IV-B); this is that idea for a stream of batches.
+//
+// Host side, a request's inputs and results pass through a pinned staging
+// arena owned by the server: a copy between the device and pageable memory
+// would block the scheduler thread until the slot's stream drained (a
+// device->host copy into pageable memory returns only once it has run), so
+// every request would wait for the previous one.  The scheduler copies the
+// inputs into the staging area before enqueueing, the stream copies the
+// results into it, and the completion callback copies them to the caller's
+// buffer.  A request whose host buffers are all pinned already, or whose
+// host bytes exceed the whole staging arena, is copied directly (for the
+// latter, with pageable buffers, the scheduler waits for its copies).
 #include <algorithm>
 #include <chrono>
 #include <condition_variable>
+#include <cstring>
 #include <deque>
 #include <map>
 #include <mutex>
@@ -95,6 +107,8 @@ struct Req {
     logan_request_t r{};
     size_t bytes = 0;
     size_t ws_bytes = 0;
+    size_t hbytes = 0;    // pinned staging bytes (0: copied directly)
+    size_t hoff = 0;
     St state = St::Queued;
     int status = LOGAN_OK;
     size_t off = 0;
@@ -112,6 +126,46 @@ size_t pool_bytes(const logan_seqs_t& p) {
     return up(b) + up(size_t(p.count) * 8) + up(size_t(p.count) * 4);
 }
 
+// bytes of the caller's pool buffer (ASCII: pool_bases bytes; packed: the
+// words up to ceil(pool_bases / 16))
+size_t pool_host_bytes(const logan_seqs_t& p) {
+    return p.packed2bit ? ((p.pool_bases + 15) / 16) * 4 : p.pool_bases;
+}
+
+size_t request_host_bytes(const logan_request_t& r) {
+    size_t b = 0;
+    for (const logan_seqs_t* p : {&r.A, &r.B}) {
+        if (p == &r.B && r.same_pool) break;
+        b += up(pool_host_bytes(*p)) + up(size_t(p->count) * 8) + up(size_t(p->count) * 4);
+    }
+    return b + up(size_t(r.n_pairs) * sizeof(logan_seed_t)) +
+           (r.X_per_pair ? up(size_t(r.n_pairs) * 4) : 0) +
+           up(size_t(r.n_pairs) * sizeof(logan_result_t));
+}
+
+bool is_pinned(const void* p) {
+    if (!p) return true;
+    cudaPointerAttributes a{};
+    if (cudaPointerGetAttributes(&a, p) != cudaSuccess) {
+        cudaGetLastError();
+        return false;
+    }
+    return a.type == cudaMemoryTypeHost;
+}
+
+bool request_pinned(const logan_request_t& r) {
+    for (const logan_seqs_t* p : {&r.A, &r.B})
+        if (!is_pinned(p->bases) || !is_pinned(p->offsets) || !is_pinned(p->lengths)) return false;
+    return is_pinned(r.seeds) && is_pinned(r.X_per_pair) && is_pinned(r.results);
+}
+
+// pinned staging capacity for a device budget: an eighth of it, within
+// [16 MiB, 1 GiB] (host bytes are the inputs and results only; the device
+// bytes also hold the workspace)
+size_t staging_bytes(size_t budget) {
+    return std::min<size_t>(std::max<size_t>(budget / 8, size_t(16) << 20), size_t(1) << 30);
+}
+
 }  // namespace
 
 struct logan_server {
@@ -119,6 +173,8 @@ struct logan_server {
     int device = 0;
     char* dev = nullptr;
     Arena arena;
+    char* host = nullptr;  // pinned staging
+    Arena harena;
     std::vector<Slot> slots;
     std::mutex mu;
     std::condition_variable cv;       // scheduler wake-up
@@ -130,6 +186,7 @@ struct logan_server {
     bool stop = false;
     std::thread th;
     uint64_t n_done = 0, n_failed = 0, n_cancelled = 0;
+    int64_t saved_opts[3] = {0, 0, 1};  // graphs, timing, concurrent: restored at destroy
 };
 
 namespace {
@@ -137,12 +194,16 @@ namespace {
 struct CbArg {
     logan_server* s;
     uint64_t ticket;
+    const void* staged_results;  // null: results were copied directly
+    void* results;
+    size_t result_bytes;
 };
 
 // host callback at the end of a request's stream work: no CUDA calls here
 void CUDART_CB on_done(void* p) {
     CbArg* a = static_cast<CbArg*>(p);
     logan_server* s = a->s;
+    if (a->staged_results) std::memcpy(a->results, a->staged_results, a->result_bytes);
     {
         std::lock_guard<std::mutex> lk(s->mu);
         auto it = s->reqs.find(a->ticket);
@@ -151,6 +212,7 @@ void CUDART_CB on_done(void* p) {
             q.state = St::Done;
             q.t_done = now_s();
             s->arena.release(q.off, q.bytes);
+            if (q.hbytes) s->harena.release(q.hoff, q.hbytes);
             s->slots[q.slot].ticket = 0;
             s->n_done++;
         }
@@ -171,6 +233,21 @@ int launch(logan_server* s, uint64_t ticket, Req& q) {
         return p;
     };
     const logan_request_t& r = q.r;
+    // host source of each copy: the pinned staging area (filled here) or,
+    // for a request too large for it, the caller's buffer itself
+    char* hbase = q.hbytes ? s->host + q.hoff : nullptr;
+    size_t hat = 0;
+    auto h2d = [&](void* dst, const void* src, size_t n) -> cudaError_t {
+        if (!n) return cudaSuccess;
+        const void* from = src;
+        if (hbase) {
+            char* h = hbase + hat;
+            hat += up(n);
+            std::memcpy(h, src, n);
+            from = h;
+        }
+        return cudaMemcpyAsync(dst, from, n, cudaMemcpyHostToDevice, st);
+    };
     auto copy_pool = [&](const logan_seqs_t& h, logan_seqs_t& d) -> cudaError_t {
         const size_t nb = h.packed2bit ? ((h.pool_bases + 15) / 16 + 1) * 4 : h.pool_bases;
         char* b = place(nb);
@@ -178,16 +255,13 @@ int launch(logan_server* s, uint64_t ticket, Req& q) {
         char* l = place(size_t(h.count) * 4);
         cudaError_t e = cudaSuccess;
         if (nb && h.bases) {
-            // the caller's buffer holds pool_bases bytes (ASCII) or the words
-            // up to ceil(pool_bases/16); the spare word is zeroed here
-            const size_t have = h.packed2bit ? ((h.pool_bases + 15) / 16) * 4 : h.pool_bases;
-            e = cudaMemcpyAsync(b, h.bases, have, cudaMemcpyHostToDevice, st);
+            // the spare word of a packed pool is zeroed here
+            const size_t have = pool_host_bytes(h);
+            e = h2d(b, h.bases, have);
             if (e == cudaSuccess && nb > have) e = cudaMemsetAsync(b + have, 0, nb - have, st);
         }
-        if (e == cudaSuccess && h.count)
-            e = cudaMemcpyAsync(o, h.offsets, size_t(h.count) * 8, cudaMemcpyHostToDevice, st);
-        if (e == cudaSuccess && h.count)
-            e = cudaMemcpyAsync(l, h.lengths, size_t(h.count) * 4, cudaMemcpyHostToDevice, st);
+        if (e == cudaSuccess && h.count) e = h2d(o, h.offsets, size_t(h.count) * 8);
+        if (e == cudaSuccess && h.count) e = h2d(l, h.lengths, size_t(h.count) * 4);
         d = h;
         d.bases = b;
         d.offsets = reinterpret_cast<const uint64_t*>(o);
@@ -204,21 +278,19 @@ int launch(logan_server* s, uint64_t ticket, Req& q) {
     char* xs = r.X_per_pair ? place(size_t(r.n_pairs) * 4) : nullptr;
     char* res = place(size_t(r.n_pairs) * sizeof(logan_result_t));
     char* ws = place(q.ws_bytes);
-    if (e == cudaSuccess)
-        e = cudaMemcpyAsync(seeds, r.seeds, size_t(r.n_pairs) * sizeof(logan_seed_t),
-                            cudaMemcpyHostToDevice, st);
-    if (e == cudaSuccess && xs)
-        e = cudaMemcpyAsync(xs, r.X_per_pair, size_t(r.n_pairs) * 4, cudaMemcpyHostToDevice, st);
+    if (e == cudaSuccess) e = h2d(seeds, r.seeds, size_t(r.n_pairs) * sizeof(logan_seed_t));
+    if (e == cudaSuccess && xs) e = h2d(xs, r.X_per_pair, size_t(r.n_pairs) * 4);
     if (e != cudaSuccess) return LOGAN_ECUDA;
     int rc = logan_extend_batch(s->ctx, &dA, &dB, reinterpret_cast<const logan_seed_t*>(seeds),
                                 r.n_pairs, r.match, r.mismatch, r.gap, r.X,
                                 reinterpret_cast<const int32_t*>(xs), ws, q.ws_bytes,
                                 reinterpret_cast<logan_result_t*>(res), st);
     if (rc != LOGAN_OK) return rc;
-    e = cudaMemcpyAsync(r.results, res, size_t(r.n_pairs) * sizeof(logan_result_t),
-                        cudaMemcpyDeviceToHost, st);
+    const size_t rbytes = size_t(r.n_pairs) * sizeof(logan_result_t);
+    void* hres = hbase ? static_cast<void*>(hbase + hat) : static_cast<void*>(r.results);
+    e = cudaMemcpyAsync(hres, res, rbytes, cudaMemcpyDeviceToHost, st);
     if (e != cudaSuccess) return LOGAN_ECUDA;
-    CbArg* a = new CbArg{s, ticket};
+    CbArg* a = new CbArg{s, ticket, hbase ? hres : nullptr, r.results, rbytes};
     if (cudaLaunchHostFunc(st, on_done, a) != cudaSuccess) {
         delete a;
         return LOGAN_ECUDA;
@@ -246,8 +318,13 @@ void scheduler(logan_server* s) {
                     slot = int(k);
                     break;
                 }
-            size_t off = 0;
+            size_t off = 0, hoff = 0;
             if (slot < 0 || !s->arena.alloc(q.bytes, &off)) break;
+            if (q.hbytes && !s->harena.alloc(q.hbytes, &hoff)) {
+                s->arena.release(off, q.bytes);
+                break;
+            }
+            q.hoff = hoff;
             s->queue.pop_front();
             q.state = St::Running;
             q.slot = slot;
@@ -267,6 +344,7 @@ void scheduler(logan_server* s) {
                 q.status = rc;
                 q.t_done = now_s();
                 s->arena.release(q.off, q.bytes);
+                if (q.hbytes) s->harena.release(q.hoff, q.hbytes);
                 s->slots[slot].ticket = 0;
                 s->n_failed++;
                 s->done_cv.notify_all();
@@ -303,6 +381,10 @@ int logan_server_create(logan_ctx_t* ctx, size_t budget_bytes, int max_inflight,
     cudaSetDevice(s->device);
     int rc = LOGAN_OK;
     if (cudaMalloc(&s->dev, budget_bytes) != cudaSuccess) rc = LOGAN_ENOMEM;
+    const size_t hsize = staging_bytes(budget_bytes);
+    if (rc == LOGAN_OK && cudaHostAlloc(reinterpret_cast<void**>(&s->host), hsize,
+                                        cudaHostAllocDefault) != cudaSuccess)
+        rc = LOGAN_ENOMEM;
     s->slots.resize(size_t(max_inflight));
     for (auto& sl : s->slots)
         if (rc == LOGAN_OK && cudaStreamCreateWithFlags(&sl.stream, cudaStreamNonBlocking) != cudaSuccess)
@@ -312,14 +394,23 @@ int logan_server_create(logan_ctx_t* ctx, size_t budget_bytes, int max_inflight,
         for (auto& sl : s->slots)
             if (sl.stream) cudaStreamDestroy(sl.stream);
         if (s->dev) cudaFree(s->dev);
+        if (s->host) cudaFreeHost(s->host);
         delete s;
         return rc;
     }
     s->arena.init(budget_bytes);
+    s->harena.init(hsize);
     // the scheduler owns the context from now on: graphs off (every request
-    // has its own pointers), no timing
+    // has its own pointers), no timing, and every request's levels on its
+    // slot stream (requests already overlap across slots; more streams per
+    // request would only share the device's hardware queues, so that a long
+    // extension in one request could hold back another request's launches)
+    logan_get_option(ctx, LOGAN_OPT_GRAPHS, &s->saved_opts[0]);
+    logan_get_option(ctx, LOGAN_OPT_TIMING, &s->saved_opts[1]);
+    logan_get_option(ctx, LOGAN_OPT_CONCURRENT, &s->saved_opts[2]);
     logan_set_option(ctx, LOGAN_OPT_GRAPHS, 0);
     logan_set_option(ctx, LOGAN_OPT_TIMING, 0);
+    logan_set_option(ctx, LOGAN_OPT_CONCURRENT, 0);
     s->th = std::thread(scheduler, s);
     *out = s;
     return LOGAN_OK;
@@ -346,6 +437,8 @@ int logan_server_submit(logan_server_t* s, const logan_request_t* r, uint64_t* t
     if (r->same_pool) q.r.B = r->A;
     q.bytes = bytes;
     q.ws_bytes = ws;
+    const size_t hb = request_host_bytes(q.r);
+    q.hbytes = (hb <= s->harena.size() && !request_pinned(q.r)) ? hb : 0;
     q.t_submit = now_s();
     s->reqs.emplace(t, q);
     s->queue.push_back(t);
@@ -448,7 +541,11 @@ int logan_server_destroy(logan_server_t* s) {
         }
     }
     cudaFree(s->dev);
+    cudaFreeHost(s->host);
     cudaSetDevice(prev);
+    logan_set_option(s->ctx, LOGAN_OPT_GRAPHS, s->saved_opts[0]);
+    logan_set_option(s->ctx, LOGAN_OPT_TIMING, s->saved_opts[1]);
+    logan_set_option(s->ctx, LOGAN_OPT_CONCURRENT, s->saved_opts[2]);
     delete s;
     return LOGAN_OK;
 }

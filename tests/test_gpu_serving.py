@@ -119,3 +119,26 @@ def test_queue_limit_cancel_and_bounded_wait(ctx):
         assert e.value.code == logan.ENOTFOUND
     finally:
         srv.close()
+
+
+@pytest.mark.parametrize("pin", [False, True])
+def test_pageable_and_pinned_requests(ctx, pin):
+    # pageable buffers go through the server's pinned staging arena, pinned
+    # ones are copied directly: the results are the same either way, and the
+    # context's options come back when the server is destroyed
+    reqs = _requests(8, seed=7)
+    alone = [_alone(ctx, b) for b in reqs]
+    ctx.set_option(logan.OPT_CONCURRENT, 1)
+    hosts = [logan.HostRequest(b, pin=pin) for b in reqs]
+    srv = logan.Server(ctx, budget_bytes=1 << 30, max_inflight=4)
+    try:
+        assert ctx.get_option(logan.OPT_CONCURRENT) == 0
+        tickets = [srv.submit(h) for h in hosts]
+        for t in tickets:
+            st, _ = srv.wait(t, timeout_ms=120_000)
+            assert st == logan.OK
+    finally:
+        srv.close()
+    assert ctx.get_option(logan.OPT_CONCURRENT) == 1
+    for h, a in zip(hosts, alone):
+        np.testing.assert_array_equal(h.result_array(), a)
