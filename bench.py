@@ -52,10 +52,12 @@ def parse():
     ap.add_argument("--pairs", type=int, default=None,
                     help="pairs per GPU (default: the workload's own size)")
     ap.add_argument("--workload", default="lognormal_batch",
-                    choices=["lognormal_batch", "uniform_pairs", "uneven_batch"],
+                    choices=["lognormal_batch", "uniform_pairs", "uneven_batch",
+                             "overlap_batch"],
                     help="lognormal_batch (default, the headline configuration), "
-                         "uniform_pairs (1,000 x 2 kbp, X = 50) or uneven_batch "
-                         "(20,000 pairs of 1 kbp-1 Mbp, X per pair)")
+                         "uniform_pairs (1,000 x 2 kbp, X = 50), uneven_batch "
+                         "(20,000 pairs of 1 kbp-1 Mbp, X per pair) or overlap_batch "
+                         "(1,000,000 overlap candidates between reads of a 50 Mbp genome)")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-e2e", action="store_true")
@@ -73,7 +75,8 @@ def parse():
     return ap.parse_args()
 
 
-DEFAULT_PAIRS = {"lognormal_batch": 100_000, "uniform_pairs": 1_000, "uneven_batch": 20_000}
+DEFAULT_PAIRS = {"lognormal_batch": 100_000, "uniform_pairs": 1_000, "uneven_batch": 20_000,
+                 "overlap_batch": 1_000_000}
 
 
 def workload(name: str, pairs: int, rank: int):
@@ -84,6 +87,9 @@ def workload(name: str, pairs: int, rank: int):
     elif name == "uneven_batch":
         b = synth.uneven_batch(n_pairs=pairs, seed=3 + 1000 * rank)
         b.meta["packed2bit"] = True
+    elif name == "overlap_batch":
+        b = synth.overlap_batch(n_pairs=pairs, seed=1 + 1000 * rank)
+        b.meta["packed2bit"] = True
     else:
         b = synth.lognormal_batch(n_pairs=pairs, seed=2 + 1000 * rank)
         b.meta["packed2bit"] = True
@@ -91,7 +97,7 @@ def workload(name: str, pairs: int, rank: int):
 
 
 def workload_config(b, name, pairs):
-    packed_mb = (b.poolA.size + b.poolB.size) // 4 / 1e6
+    packed_mb = b.pool_bases / 4 / 1e6
     common = {"scoring": [1, -1, -1], "seed_len": 17,
               "parallelism": "replicas (independent pairs per GPU, no collective)"}
     if name == "uniform_pairs":
@@ -106,6 +112,15 @@ def workload_config(b, name, pairs):
                 "error_rate": "U[0.05, 0.20] per pair", "X": "per pair from {10,50,100,500}",
                 "input": "2-bit packed",
                 "l2": f"inputs larger than L2 (packed pools {packed_mb:.0f} MB), no flush", **common}
+    if name == "overlap_batch":
+        return {"workload": name, "pairs": pairs, "genome_bp": b.meta["genome_len"],
+                "reads": b.meta["n_reads"], "read_len": "lognormal, mean 10 kbp, sigma 0.5",
+                "strand": "reverse with p = 0.5",
+                "errors": "12 % (6 % ins, 4 % del, 2 % sub)",
+                "true_overlaps": 0.3, "spurious": "0.7, one planted shared 17-mer (B copied)",
+                "X": 50, "input": "2-bit packed, one shared pool",
+                "l2": f"inputs larger than L2 (packed pool {packed_mb:.0f} MB), no flush",
+                **common}
     return {"workload": name, "pairs": pairs, "median_len": 10_000,
             "len_sigma": 0.5, "len_clip": [1000, 30000], "related_frac": 0.8,
             "error_rate": 0.12, "X": 100, "input": "2-bit packed",
@@ -334,7 +349,7 @@ def main():
 
     # inputs smaller than L2 (129 MB): flush L2 between timed steps by writing a
     # 512 MB buffer, outside each step's own pair of events
-    small = (b.poolA.size + (0 if b.shared_pool else b.poolB.size)) // (4 if packed else 1) < (256 << 20)
+    small = b.pool_bases // (4 if packed else 1) < (256 << 20)
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}") if small else None
 
     def timed(fn, steps, warmup):
@@ -435,29 +450,34 @@ def main():
         # extend -> results back to pinned host memory, every step
         hA = {k: v.cpu().pin_memory() for k, v in (("bases", A.bases), ("off", A.offsets),
                                                    ("len", A.lengths))}
-        hB = {k: v.cpu().pin_memory() for k, v in (("bases", B.bases), ("off", B.offsets),
-                                                   ("len", B.lengths))}
+        shared = B is A  # one pool serves both sides: copied once
+        hB = hA if shared else {k: v.cpu().pin_memory() for k, v in (
+            ("bases", B.bases), ("off", B.offsets), ("len", B.lengths))}
         hS = S.cpu().pin_memory()
         hX = Xs.cpu().pin_memory() if Xs is not None else None
         hout = torch.empty_like(out, device="cpu").pin_memory()
         dA = logan.DevicePool(torch.empty_like(A.bases), torch.empty_like(A.offsets),
                               torch.empty_like(A.lengths), packed, A.pool_bases)
-        dB = logan.DevicePool(torch.empty_like(B.bases), torch.empty_like(B.offsets),
-                              torch.empty_like(B.lengths), packed, B.pool_bases)
+        dB = dA if shared else logan.DevicePool(
+            torch.empty_like(B.bases), torch.empty_like(B.offsets), torch.empty_like(B.lengths),
+            packed, B.pool_bases)
         dS = torch.empty_like(S)
-        h2d = sum(t.numel() * t.element_size() for t in list(hA.values()) + list(hB.values()) + [hS])
+        dX = torch.empty_like(Xs) if Xs is not None else None
+        h2d = sum(t.numel() * t.element_size()
+                  for t in list(hA.values()) + ([] if shared else list(hB.values())) + [hS] +
+                  ([hX] if hX is not None else []))
         d2h = hout.numel() * hout.element_size()
 
         def e2e_step():
             with torch.cuda.stream(stream):
-                dA.bases.copy_(hA["bases"], non_blocking=True)
-                dA.offsets.copy_(hA["off"], non_blocking=True)
-                dA.lengths.copy_(hA["len"], non_blocking=True)
-                dB.bases.copy_(hB["bases"], non_blocking=True)
-                dB.offsets.copy_(hB["off"], non_blocking=True)
-                dB.lengths.copy_(hB["len"], non_blocking=True)
+                for h, d in ((hA, dA),) if shared else ((hA, dA), (hB, dB)):
+                    d.bases.copy_(h["bases"], non_blocking=True)
+                    d.offsets.copy_(h["off"], non_blocking=True)
+                    d.lengths.copy_(h["len"], non_blocking=True)
                 dS.copy_(hS, non_blocking=True)
-                ctx.extend(dA, dB, dS, b.match, b.mismatch, b.gap, b.X, Xs, workspace=ws,
+                if dX is not None:
+                    dX.copy_(hX, non_blocking=True)
+                ctx.extend(dA, dB, dS, b.match, b.mismatch, b.gap, b.X, dX, workspace=ws,
                            out=out, stream=stream)
                 hout.copy_(out, non_blocking=True)
 

@@ -234,11 +234,12 @@ int logan_num_levels(void);
 int logan_level_info(int level, int *window_cells, int *threads_per_unit);
 
 /* Statistics of the last batch call made with LOGAN_OPT_TIMING = 1 (the
- * call records CUDA events around every extension level on its stream; this
- * function synchronises on them and reads the level counters from the
- * workspace, which must not have been reused since).
+ * call records CUDA events around every extension launch and copies its
+ * level counters to pinned host memory at its end; this function
+ * synchronises on those events).
  *   level_ms[k]  device time of window level k (k < logan_num_levels()):
- *                its phase-1 launch plus its phase-2 launch; with
+ *                its phase-1 launch plus its phase-2 launch, each counted
+ *                only if it had entries to process; with
  *                LOGAN_OPT_CONCURRENT the phase-1 launches overlap, so the
  *                levels' times can add up to more than total_ms;
  *                level_ms[logan_num_levels()] = the global-memory fallback;
@@ -258,9 +259,7 @@ typedef struct {
     uint32_t launches;
 } logan_stats_t;
 int logan_last_stats(logan_ctx_t *ctx, logan_stats_t *stats);
-/* The same for an earlier timed call: back = 0 is the last one, up to 31.
- * For back > 0 only the times and `launches` are filled (items/cells are 0:
- * the counters they come from have been overwritten). */
+/* The same for an earlier timed call: back = 0 is the last one, up to 31. */
 int logan_call_stats(logan_ctx_t *ctx, int back, logan_stats_t *stats);
 
 /* Instruction-throughput microbenchmark on `device` (the ALU roofline's

@@ -134,6 +134,9 @@ def batch(poolA: np.ndarray, offA: np.ndarray, lenA: np.ndarray,
 
 
 def run_batch(b, threads: Optional[int] = None):
-    """Convenience wrapper for a synth.Batch-like object."""
+    """Convenience wrapper for a synth.Batch-like object (ASCII pools; take
+    a subset of a packed batch first)."""
+    if getattr(b, "packed", False):
+        raise ValueError("the oracle reads ASCII pools: use b.subset(...) of a packed batch")
     return batch(b.poolA, b.offA, b.lenA, b.poolB, b.offB, b.lenB, b.seeds, b.match,
                  b.mismatch, b.gap, b.X, b.Xs, threads)

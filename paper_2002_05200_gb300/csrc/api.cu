@@ -67,8 +67,10 @@ struct logan_ctx {
         uint32_t launches = 0;
         uint32_t p1_levels = 0;  // bit l: phase-1 events of level l recorded
         uint32_t p2_levels = 0;
-        Counters* counters = nullptr;
+        bool plain = false;
     } calls[kEvSets];
+    // the level counters of each timed call, copied back at its end
+    Counters* hcounters = nullptr;  // pinned, kEvSets entries
     int64_t concurrent = 1;  // run the start levels of a batch concurrently
     std::vector<AuxSet> aux;
     bool timing_pending = false;
@@ -330,14 +332,17 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     launches += 2;  // ring + combine
     c->launches_last = launches;
     if (timing) {
-        if (!rec(EV_END, s)) return LOGAN_ECUDA;
+        if (cudaMemcpyAsync(&c->hcounters[c->timed_calls % kEvSets], counters, sizeof(Counters),
+                            cudaMemcpyDeviceToHost, s) != cudaSuccess ||
+            !rec(EV_END, s))
+            return LOGAN_ECUDA;
         auto& ci = c->calls[c->timed_calls % kEvSets];
         ci.first_level = plain ? first : 0;
         ci.max_level = maxl;
         ci.launches = launches;
         ci.p1_levels = p1_levels;
         ci.p2_levels = p2_levels;
-        ci.counters = counters;
+        ci.plain = plain != 0;
         c->timed_calls += 1;
         c->timing_pending = true;
     }
@@ -499,6 +504,11 @@ int logan_ctx_create(logan_ctx_t** out, int device, const char* autotune_json) {
                 logan_ctx_destroy(c);
                 return LOGAN_ECUDA;
             }
+    if (cudaHostAlloc(reinterpret_cast<void**>(&c->hcounters), sizeof(Counters) * kEvSets,
+                      cudaHostAllocDefault) != cudaSuccess) {
+        logan_ctx_destroy(c);
+        return LOGAN_ECUDA;
+    }
     if (autotune_json) {
         int rc = load_table_json(c, autotune_json);
         if (rc) {
@@ -528,6 +538,7 @@ void logan_ctx_destroy(logan_ctx_t* c) {
     for (auto& set : c->evs)
         for (auto& ev : set)
             if (ev) cudaEventDestroy(ev);
+    if (c->hcounters) cudaFreeHost(c->hcounters);
     delete c;
 }
 
@@ -619,14 +630,17 @@ int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
     const auto& ci = c->calls[call % kEvSets];
     if (cudaEventSynchronize(ev[EV_END]) != cudaSuccess) return LOGAN_ECUDA;
     std::memset(st, 0, sizeof(*st));
+    const Counters& h = c->hcounters[call % kEvSets];
+    // a launch counts only if it had entries to process: an empty launch's
+    // span is mostly its wait for room on the SMs
     for (int l = 0; l < kNumLevels; ++l) {
         float ms = 0.f;
-        if ((ci.p1_levels >> l) & 1u) {
+        if (((ci.p1_levels >> l) & 1u) && (h.started[l] > 0 || ci.plain)) {
             if (cudaEventElapsedTime(&ms, ev[EV_P1S + l], ev[EV_P1E + l]) != cudaSuccess)
                 return LOGAN_ECUDA;
             st->level_ms[l] += ms;
         }
-        if ((ci.p2_levels >> l) & 1u) {
+        if (((ci.p2_levels >> l) & 1u) && h.tail[l] > h.started[l]) {
             if (cudaEventElapsedTime(&ms, ev[EV_P2S + l], ev[EV_P2E + l]) != cudaSuccess)
                 return LOGAN_ECUDA;
             st->level_ms[l] += ms;
@@ -636,15 +650,9 @@ int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
         return LOGAN_ECUDA;
     if (cudaEventElapsedTime(&st->total_ms, ev[EV_START], ev[EV_END]) != cudaSuccess)
         return LOGAN_ECUDA;
-    if (back == 0) {
-        // the level counters live in the workspace: valid for the last call only
-        Counters h;
-        if (cudaMemcpy(&h, ci.counters, sizeof(h), cudaMemcpyDeviceToHost) != cudaSuccess)
-            return LOGAN_ECUDA;
-        for (int l = 0; l <= kNumLevels; ++l) {
-            st->items[l] = h.tail[l];
-            st->cells[l] = h.cells[l];
-        }
+    for (int l = 0; l <= kNumLevels; ++l) {
+        st->items[l] = h.tail[l];
+        st->cells[l] = h.cells[l];
     }
     st->launches = ci.launches;
     return LOGAN_OK;

@@ -326,8 +326,12 @@ def batch_to_device(b, packed2bit: Optional[bool] = None, device="cuda"):
     import torch
     from . import synth
     packed = bool(b.meta.get("packed2bit", False)) if packed2bit is None else packed2bit
+    if b.packed and not packed:
+        raise ValueError("this batch exists only 2-bit packed")
 
     def pool(p, off, ln):
+        if b.packed:
+            return pool_to_device(p, off, ln, True, (p.size - 1) * 16, device)
         if packed:
             return pool_to_device(synth.pack2bit(p), off, ln, True, p.size, device)
         return pool_to_device(p, off, ln, False, p.size, device)
@@ -351,10 +355,17 @@ class HostRequest:
                                  else np.ascontiguousarray(a, dtype=dtype))
             return x.pin_memory() if pin else x
 
+        if b.packed and not packed2bit:
+            raise ValueError("this batch exists only 2-bit packed")
+
         def pool(p, off, ln):
-            bases = synth.pack2bit(p).view(np.int32) if packed2bit else p
+            if b.packed:
+                bases, nb = p.view(np.int32), (p.size - 1) * 16
+            else:
+                bases = synth.pack2bit(p).view(np.int32) if packed2bit else p
+                nb = int(p.size)
             return (t(bases), t(np.ascontiguousarray(off, np.uint64).view(np.int64)),
-                    t(np.ascontiguousarray(ln, np.uint32).view(np.int32)), int(p.size))
+                    t(np.ascontiguousarray(ln, np.uint32).view(np.int32)), nb)
 
         self.batch = b
         self.n_pairs = b.n_pairs

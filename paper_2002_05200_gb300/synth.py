@@ -23,8 +23,16 @@ Workloads (sizes are parameters so tests can draw small copies):
   error rate U[5 %, 20 %] per pair, X drawn per pair from {10,50,100,500}.
 * ``serving_requests`` -- Poisson arrivals of requests whose pairs follow
   the uneven mixture, X = 50.
+* ``overlap_batch``  -- many-to-many overlap candidates: 50,000 reads
+  sampled from a random 50 Mbp genome (lognormal lengths, mean 10 kbp,
+  sigma 0.5; reverse strand with p = 0.5; 12 % errors as 6 % insertions,
+  4 % deletions, 2 % substitutions), 1,000,000 candidate pairs: 30 % true
+  overlaps seeded at the shared exact 17-mer nearest the overlap centre,
+  70 % spurious pairs carrying one planted shared 17-mer, X = 50.  Its pool
+  is built 2-bit packed (about 2 GB) and never exists as ASCII.
 
-Sequences are uint8 ASCII ('A','C','G','T').  ``pack2bit`` converts a pool
+Sequences are uint8 ASCII ('A','C','G','T'), except in a batch built
+packed (``Batch.packed``).  ``pack2bit`` converts a pool
 to the 2-bit packed input format of the library (A0 C1 G2 T3, 16 bases per
 little-endian uint32 word, base k of the pool at word k//16, bits
 2*(k%16)..2*(k%16)+1); it is a storage format, not part of the method.
@@ -51,7 +59,9 @@ _CHUNK_BASES = 1 << 24
 class Batch:
     """A batch of seeded pairs.
 
-    poolA/poolB: uint8 ASCII bases of all sequences, concatenated.
+    poolA/poolB: uint8 ASCII bases of all sequences, concatenated; or, when
+                 `packed`, the uint32 words of the 2-bit packed pool (see
+                 pack2bit), including its spare word.
     offA/offB:   uint64 base offset of each sequence in its pool.
     lenA/lenB:   uint32 length of each sequence.
     seeds:       SEED_DTYPE records, one per pair (indices into the pools).
@@ -72,29 +82,63 @@ class Batch:
     gap: int = -1
     shared_pool: bool = False
     meta: dict = field(default_factory=dict)
+    packed: bool = False
 
     @property
     def n_pairs(self) -> int:
         return int(self.seeds.shape[0])
 
+    def _seq(self, pool, off, ln, i) -> bytes:
+        o, n = int(off[i]), int(ln[i])
+        if self.packed:
+            return unpack2bit(pool, o, n).tobytes()
+        return pool[o:o + n].tobytes()
+
     def seqA(self, p: int) -> bytes:
-        s = self.seeds[p]
-        o, n = int(self.offA[s["idxA"]]), int(self.lenA[s["idxA"]])
-        return self.poolA[o:o + n].tobytes()
+        return self._seq(self.poolA, self.offA, self.lenA, self.seeds[p]["idxA"])
 
     def seqB(self, p: int) -> bytes:
-        s = self.seeds[p]
-        o, n = int(self.offB[s["idxB"]]), int(self.lenB[s["idxB"]])
-        return self.poolB[o:o + n].tobytes()
+        return self._seq(self.poolB, self.offB, self.lenB, self.seeds[p]["idxB"])
+
+    @property
+    def pool_bases(self) -> int:
+        """Bases the pools span (packed: whole words, without the spare)."""
+        if self.packed:
+            n = (self.poolA.size - 1) * 16
+            return n if self.shared_pool else n + (self.poolB.size - 1) * 16
+        return int(self.poolA.size) + (0 if self.shared_pool else int(self.poolB.size))
 
     def subset(self, idx) -> "Batch":
-        """Pairs `idx` only (pools are shared, not copied)."""
+        """Pairs `idx` only.  ASCII pools are shared, not copied; a packed
+        batch gives an ASCII batch holding just the sequences those pairs
+        use (small enough for the CPU oracle)."""
         idx = np.asarray(idx)
-        return Batch(self.name + "[sub]", self.poolA, self.offA, self.lenA,
-                     self.poolB, self.offB, self.lenB, self.seeds[idx].copy(),
-                     self.X, None if self.Xs is None else self.Xs[idx].copy(),
-                     self.match, self.mismatch, self.gap, self.shared_pool,
-                     dict(self.meta))
+        sd = self.seeds[idx].copy()
+        Xs = None if self.Xs is None else self.Xs[idx].copy()
+        if not self.packed:
+            return Batch(self.name + "[sub]", self.poolA, self.offA, self.lenA,
+                         self.poolB, self.offB, self.lenB, sd, self.X, Xs,
+                         self.match, self.mismatch, self.gap, self.shared_pool,
+                         dict(self.meta))
+
+        def gather(pool, off, ln, ids):
+            u, inv = np.unique(ids, return_inverse=True)
+            lens = ln[u].astype(np.uint32)
+            parts = [unpack2bit(pool, int(off[i]), int(ln[i])) for i in u]
+            asc = np.concatenate(parts) if parts else np.zeros(0, np.uint8)
+            return asc, _offsets(lens), lens, inv.astype(np.uint32)
+
+        if self.shared_pool:
+            both = np.concatenate([sd["idxA"], sd["idxB"]])
+            pool, off, ln, inv = gather(self.poolA, self.offA, self.lenA, both)
+            sd["idxA"], sd["idxB"] = inv[:idx.size], inv[idx.size:]
+            return Batch(self.name + "[sub]", pool, off, ln, pool, off, ln, sd, self.X, Xs,
+                         self.match, self.mismatch, self.gap, True, dict(self.meta))
+        pa, oa, la, ia = gather(self.poolA, self.offA, self.lenA, sd["idxA"])
+        pb, ob, lb, ib = gather(self.poolB, self.offB, self.lenB, sd["idxB"])
+        sd["idxA"], sd["idxB"] = ia, ib
+        return Batch(self.name + "[sub]", pa, oa, la, pb, ob, lb, sd, self.X, Xs,
+                     self.match, self.mismatch, self.gap, False, dict(self.meta))
 
     @property
     def total_bases(self) -> int:
@@ -104,23 +148,43 @@ class Batch:
         return n
 
 
+_SHIFTS16 = (2 * np.arange(16, dtype=np.uint32))
+_CODE_LUT = np.zeros(256, dtype=np.uint8)
+_CODE_LUT[ord("C")] = 1
+_CODE_LUT[ord("G")] = 2
+_CODE_LUT[ord("T")] = 3
+
+
 def pack2bit(pool: np.ndarray) -> np.ndarray:
     """ASCII pool -> uint32 words, 16 bases per word, A0 C1 G2 T3.
 
     The pool is padded with 'A' codes to a whole number of words plus one
-    spare word (readers may fetch one word past the last base).
+    spare word (readers may fetch one word past the last base).  Works in
+    chunks, so host memory stays near the pool's own size.
     """
-    lut = np.full(256, 0, dtype=np.uint8)
-    lut[ord("C")] = 1
-    lut[ord("G")] = 2
-    lut[ord("T")] = 3
-    codes = lut[pool]
-    nw = (codes.size + 15) // 16 + 1
-    padded = np.zeros(nw * 16, dtype=np.uint32)
-    padded[:codes.size] = codes
-    padded = padded.reshape(nw, 16)
-    shifts = (2 * np.arange(16, dtype=np.uint32))
-    return np.bitwise_or.reduce(padded << shifts, axis=1).astype(np.uint32)
+    n = int(pool.size)
+    out = np.zeros((n + 15) // 16 + 1, dtype=np.uint32)
+    step = 1 << 24  # bases per chunk, a multiple of 16
+    for s0 in range(0, n, step):
+        m = min(step, n - s0)
+        c = np.zeros((m + 15) // 16 * 16, dtype=np.uint8)
+        c[:m] = _CODE_LUT[pool[s0:s0 + m]]
+        q = c.reshape(-1, 4)
+        # byte j holds bases 4j..4j+3; four bytes make one little-endian word
+        by = q[:, 0] | (q[:, 1] << 2) | (q[:, 2] << 4) | (q[:, 3] << 6)
+        w = by.view("<u4")
+        out[s0 // 16:s0 // 16 + w.size] = w
+    return out
+
+
+def unpack2bit(words: np.ndarray, off: int, n: int) -> np.ndarray:
+    """Bases [off, off + n) of a packed pool, as ASCII."""
+    if n <= 0:
+        return np.zeros(0, dtype=np.uint8)
+    w0, w1 = off // 16, (off + n + 15) // 16
+    codes = ((words[w0:w1, None] >> _SHIFTS16) & 3).astype(np.uint8).ravel()
+    s0 = off - 16 * w0
+    return ASCII[codes[s0:s0 + n]]
 
 
 def _offsets(lengths: np.ndarray) -> np.ndarray:
@@ -128,9 +192,6 @@ def _offsets(lengths: np.ndarray) -> np.ndarray:
     if lengths.size > 1:
         np.cumsum(lengths[:-1], dtype=np.uint64, out=off[1:])
     return off
-
-
-_SHIFTS16 = (2 * np.arange(16, dtype=np.uint32))
 
 
 def _random_bases(rng: np.random.Generator, n: int) -> np.ndarray:
@@ -161,14 +222,17 @@ def _error_positions(rng, n: int, err_p) -> np.ndarray:
     return np.flatnonzero(u < err_p)
 
 
-def _mutate_chunk(rng, src: np.ndarray, err_p, protect_idx: np.ndarray, type_p: tuple):
+def _mutate_chunk(rng, src: np.ndarray, err_p, protect_idx: np.ndarray, type_p: tuple,
+                  events: bool = False):
     """Edit walk over `src` (ASCII, one chunk).
 
     Each base outside `protect_idx` suffers an error with probability err_p
     (a scalar, or one value per base); the error is a substitution (uniform
     other base), an insertion (a uniform base placed before it) or a deletion,
     with probabilities type_p.  Returns the output bases and, per source base,
-    the number of output bases it made.
+    the cumulative number of output bases up to and including it; with
+    `events`, also the sorted source positions of the substitutions,
+    insertions (a base inserted before the position) and deletions.
     """
     n = src.size
     err = _error_positions(rng, n, err_p)
@@ -193,6 +257,8 @@ def _mutate_chunk(rng, src: np.ndarray, err_p, protect_idx: np.ndarray, type_p: 
     lut[ASCII] = np.arange(4, dtype=np.uint8)
     code = (lut[src[sub]] + rng.integers(1, 4, size=sub.size, dtype=np.uint8)) & 3
     out[csum[sub] - 1] = ASCII[code]
+    if events:
+        return out, csum, (sub, ins, dele)
     return out, csum
 
 
@@ -411,3 +477,223 @@ def tiny_pairs(n_pairs: int, max_len: int, seed: int, alphabet: bytes = b"ACGT",
     Xs = np.asarray(X_choices, dtype=np.int32)[rng.integers(0, len(X_choices), size=n_pairs)]
     return Batch("tiny_pairs", poolA, _offsets(lenA), lenA, poolB, _offsets(lenB), lenB,
                  seeds, int(max(X_choices)), Xs=Xs, meta=dict(seed=seed, max_len=max_len))
+
+
+# ---------------------------------------------------------------------------
+# many-to-many overlap candidates
+
+OVERLAP_TYPES = (2 / 12, 6 / 12, 4 / 12)  # (sub, ins, del) shares of the errors
+_COMP = np.zeros(256, dtype=np.uint8)
+_COMP[np.frombuffer(b"ACGT", np.uint8)] = np.frombuffer(b"TGCA", np.uint8)
+_KEY_SHIFT = 27  # event key = read << 27 | genome position (genome < 2^27 bases)
+
+
+def _count_in(keys: np.ndarray, r: np.ndarray, g0: np.ndarray, g1: np.ndarray) -> np.ndarray:
+    """Events of read r at genome positions [g0, g1] (vectorised)."""
+    base = r.astype(np.int64) << _KEY_SHIFT
+    return (np.searchsorted(keys, base | g1.astype(np.int64), side="right") -
+            np.searchsorted(keys, base | g0.astype(np.int64), side="left"))
+
+
+def _read_pos(r, g, starts, ins_keys, del_keys):
+    """Index in the forward-oriented read r of the kept genome base g: its
+    offset, plus the bases inserted at or before it, minus those deleted
+    before it."""
+    rr = np.asarray(r, np.int64)
+    gg = np.asarray(g, np.int64)
+    lo = np.zeros_like(gg)
+    n_ins = _count_in(ins_keys, rr, starts[rr] + lo, gg)
+    n_del = _count_in(del_keys, rr, starts[rr] + lo, gg - 1)
+    return gg - starts[rr] + n_ins - n_del
+
+
+def overlap_batch(n_pairs: int = 1_000_000, n_reads: int = 50_000,
+                  genome_len: int = 50_000_000, mean_len: int = 10_000, sigma: float = 0.5,
+                  true_frac: float = 0.3, err: float = 0.12, type_p=OVERLAP_TYPES,
+                  X: int = 50, seed: int = 1, min_len: int = 1_000) -> Batch:
+    """Overlap candidates between reads of one random genome.
+
+    Genome: uniform ACGT of genome_len bases.  Reads: lognormal lengths with
+    the given mean (mu = ln(mean) - sigma^2/2), clipped to [min_len,
+    genome_len], uniform start, edit walk at rate `err` split by `type_p`
+    (sub, ins, del), reverse-complemented with p = 0.5.  The pool holds every
+    read as sequenced (index 2r) and its reverse complement (2r + 1), each
+    starting on a 16-base boundary, then one copy per spurious pair.
+
+    True overlaps (true_frac of the pairs): read a uniform, read b uniform
+    among the reads whose start lies in a's window, kept when the genome
+    intervals share at least 17 bases.  B is b in a's orientation; the seed is
+    the genome 17-mer that both reads hold exactly (no substitution or
+    deletion in it, no insertion inside it) nearest the centre of the
+    overlap, ties to the right; a pair without one is drawn again.
+    Spurious pairs: reads a, b with disjoint intervals; B is a copy of b with
+    the 17-mer of a at a uniform position written over a uniform position.
+    """
+    assert genome_len < (1 << _KEY_SHIFT)
+    rng = np.random.default_rng([seed, 0])
+    genome = _random_bases(rng, genome_len)
+    mu = np.log(mean_len) - sigma * sigma / 2
+    rl = np.clip(np.rint(rng.lognormal(mu, sigma, size=n_reads)), max(min_len, SEED_LEN),
+                 genome_len).astype(np.int64)
+    rs = rng.integers(0, genome_len - rl + 1).astype(np.int64)
+    rev = rng.random(n_reads) < 0.5
+
+    # edit walks, one chunk of reads per random stream
+    def walk(ci, r0, r1):
+        g = np.random.default_rng([seed, 1, ci])
+        lens = rl[r0:r1]
+        src = np.concatenate([genome[a:a + n] for a, n in zip(rs[r0:r1], lens)])
+        out, csum, ev = _mutate_chunk(g, src, np.float32(err), np.zeros(0, np.int64), type_p,
+                                      events=True)
+        st = _offsets(lens).astype(np.int64)
+        before = np.where(st > 0, csum[np.maximum(st - 1, 0)], 0)
+        olen = csum[st + lens - 1] - before
+        keys = []
+        n = src.size
+        kill = np.zeros(n + 1, dtype=np.int32)
+        for t, e in enumerate(ev):
+            rr = np.searchsorted(st, e, side="right") - 1
+            keys.append(((rr + r0).astype(np.int64) << _KEY_SHIFT) | (rs[r0 + rr] + e - st[rr]))
+            # window starts this event spoils: [e-16, e] for a substitution or
+            # deletion, [e-16, e-1] for an insertion (placed before base e)
+            lo = np.maximum(e - (SEED_LEN - 1), st[rr])
+            hi = e if t != 1 else e - 1
+            ok = hi >= lo
+            kill += np.bincount(lo[ok], minlength=n + 1).astype(np.int32)
+            kill -= np.bincount(hi[ok] + 1, minlength=n + 1).astype(np.int32)
+        clean = np.cumsum(kill[:n], dtype=np.int32) == 0
+        return out, olen, keys, clean
+
+    res = _parallel(walk, [(ci, a, b) for ci, (a, b) in enumerate(_chunks(rl))])
+    fwd = np.concatenate([x[0] for x in res])
+    flen = np.concatenate([x[1] for x in res]).astype(np.int64)
+    sub_k, ins_k, del_k = (np.concatenate([x[2][t] for x in res]) for t in range(3))
+    clean = np.concatenate([x[3] for x in res])  # per genome base of each read's span
+    coff = _offsets(rl).astype(np.int64)
+    foff = _offsets(flen).astype(np.int64)
+    del res, sub_k
+
+    # true overlaps: draw, then look for a seed; redraw the pairs that have none
+    n_true = int(round(true_frac * n_pairs))
+    order = np.argsort(rs, kind="stable")
+    ss = rs[order]
+    Lmax = int(rl.max())
+    ta = np.zeros(0, np.int64)
+    tb = np.zeros(0, np.int64)
+    tp = np.zeros(0, np.int64)
+    while ta.size < n_true:
+        need = n_true - ta.size
+        a = rng.integers(0, n_reads, size=4 * need + 64)
+        lo = np.searchsorted(ss, rs[a] - Lmax, side="left")
+        hi = np.searchsorted(ss, rs[a] + rl[a], side="left")
+        b = order[np.minimum(lo + (rng.random(a.size) * (hi - lo)).astype(np.int64), n_reads - 1)]
+        o0 = np.maximum(rs[a], rs[b])
+        o1 = np.minimum(rs[a] + rl[a], rs[b] + rl[b])
+        ok = (b != a) & (o1 - o0 >= SEED_LEN)
+        a, b, o0, o1 = a[ok], b[ok], o0[ok], o1[ok]
+        # nearest clean 17-mer to the centre: offsets 0, +1, -1, +2, ... in blocks
+        c = (o0 + o1 - SEED_LEN) // 2
+        found = np.full(a.size, -1, np.int64)
+        todo = np.arange(a.size)
+        span = int((o1 - o0).max()) if a.size else 0
+        block = 64
+        for k0 in range(0, 2 * span + 2, block):
+            if todo.size == 0:
+                break
+            ks = np.arange(k0, k0 + block)
+            delta = np.where(ks % 2 == 1, (ks + 1) // 2, -(ks // 2))
+            p = c[todo, None] + delta[None, :]
+            valid = (p >= o0[todo, None]) & (p <= o1[todo, None] - SEED_LEN)
+            both = valid.copy()
+            for r in (a[todo], b[todo]):
+                idx = coff[r][:, None] + (p - rs[r][:, None])
+                both &= clean[np.where(valid, idx, 0)]
+            hit = both.any(axis=1)
+            first = np.argmax(both, axis=1)
+            found[todo[hit]] = p[hit, first[hit]]
+            todo = todo[~hit]
+        good = found >= 0
+        take = np.flatnonzero(good)[:need]
+        ta = np.concatenate([ta, a[take]])
+        tb = np.concatenate([tb, b[take]])
+        tp = np.concatenate([tp, found[take]])
+
+    # seed coordinates in the forward-oriented reads, then in the stored ones
+    qa = _read_pos(ta, tp, rs, ins_k, del_k)
+    qb = _read_pos(tb, tp, rs, ins_k, del_k)
+    ra = rev[ta]
+    posA_t = np.where(ra, flen[ta] - qa - SEED_LEN, qa)
+    posB_t = np.where(ra, flen[tb] - qb - SEED_LEN, qb)
+    # B in a's orientation: b as sequenced when the strands agree
+    idxB_t = 2 * tb + (rev[ta] != rev[tb])
+    idxA_t = 2 * ta
+
+    # pool of the oriented reads: 2r = as sequenced, 2r + 1 = reverse complement
+    slen = np.repeat(flen, 2)
+    pad = (slen + 15) // 16 * 16
+    soff = _offsets(pad).astype(np.int64)
+    asc = np.full(int(pad.sum()), ord("A"), dtype=np.uint8)
+    rcpool = _COMP[fwd[::-1]]  # read r's reverse complement ends where r starts
+    tot = fwd.size
+    for r in range(n_reads):
+        f = fwd[foff[r]:foff[r] + flen[r]]
+        rc = rcpool[tot - foff[r] - flen[r]:tot - foff[r]]
+        s_, o_ = (rc, f) if rev[r] else (f, rc)
+        asc[soff[2 * r]:soff[2 * r] + flen[r]] = s_
+        asc[soff[2 * r + 1]:soff[2 * r + 1] + flen[r]] = o_
+    del fwd, rcpool, clean
+    words = pack2bit(asc)
+    del asc
+
+    # spurious pairs: disjoint intervals, B = copy of b with a planted 17-mer
+    n_sp = n_pairs - n_true
+    sa = np.zeros(0, np.int64)
+    sb = np.zeros(0, np.int64)
+    while sa.size < n_sp:
+        need = n_sp - sa.size
+        a = rng.integers(0, n_reads, size=need + 64)
+        b = rng.integers(0, n_reads, size=need + 64)
+        ok = (np.minimum(rs[a] + rl[a], rs[b] + rl[b]) <= np.maximum(rs[a], rs[b]))
+        sa = np.concatenate([sa, a[ok][:need]])
+        sb = np.concatenate([sb, b[ok][:need]])
+    src = 2 * sb
+    cw = pad[src] // 16
+    coff_w = words.size - 1 + _offsets(cw).astype(np.int64)  # copies start after the spare word's slot
+    parts = [words[:-1]]
+    w_of = soff // 16
+    parts += [words[w_of[i]:w_of[i] + n] for i, n in zip(src, cw)]
+    parts.append(np.zeros(1, np.uint32))
+    words = np.concatenate(parts)
+    del parts
+    posA_s = rng.integers(0, slen[2 * sa] - SEED_LEN + 1)
+    posB_s = rng.integers(0, slen[src] - SEED_LEN + 1)
+    abase = soff[2 * sa] + posA_s
+    cbase = coff_w * 16 + posB_s
+    for t in range(SEED_LEN):
+        pa_ = abase + t
+        code = (words[pa_ >> 4] >> ((pa_ & 15) * 2).astype(np.uint32)) & np.uint32(3)
+        pc = cbase + t
+        sh = ((pc & 15) * 2).astype(np.uint32)
+        wi = pc >> 4
+        words[wi] = (words[wi] & ~(np.uint32(3) << sh)) | (code << sh)
+
+    off = np.concatenate([soff, coff_w * 16]).astype(np.uint64)
+    lens = np.concatenate([slen, slen[src]]).astype(np.uint32)
+    idxB_s = 2 * n_reads + np.arange(n_sp)
+    seeds = np.zeros(n_pairs, dtype=SEED_DTYPE)
+    is_true = np.zeros(n_pairs, dtype=bool)
+    perm = rng.permutation(n_pairs)
+    tsel, ssel = perm[:n_true], perm[n_true:]
+    is_true[tsel] = True
+    seeds["idxA"][tsel], seeds["idxB"][tsel] = idxA_t, idxB_t
+    seeds["posA"][tsel], seeds["posB"][tsel] = posA_t, posB_t
+    seeds["idxA"][ssel], seeds["idxB"][ssel] = 2 * sa, idxB_s
+    seeds["posA"][ssel], seeds["posB"][ssel] = posA_s, posB_s
+    seeds["len"] = SEED_LEN
+    return Batch("overlap_batch", words, off, lens, words, off, lens, seeds, X,
+                 shared_pool=True, packed=True,
+                 meta=dict(n_pairs=n_pairs, n_reads=n_reads, genome_len=genome_len,
+                           mean_len=mean_len, sigma=sigma, err=err, seed=seed,
+                           is_true=is_true, true_genome_pos=(tsel, tp),
+                           read_start=rs, read_len=rl, read_rev=rev,
+                           genome=genome if genome_len <= (1 << 22) else None))
