@@ -39,6 +39,14 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "X-drop GCUPS (computed cells), batched vs plain launch; serving p50/p99 ms"
+# DRAM traffic of the level-2 kernel (k_group<8, 16>) from one ncu capture
+# (dram__bytes_read.sum + dram__bytes_write.sum of its launch on the
+# 24,000-pair lognormal batch, which starts 48,000 extensions there).  Scaled
+# to a launch by the extensions it starts; reported only while the kernel's
+# sources are the ones captured.
+PROFILED_TRAFFIC = {"level": 2, "bytes": 115.087104e6 + 7.610368e6, "items": 48_000,
+                    "sources": ("xdrop_group.cu", "logan_dev.cuh", "internal.h"),
+                    "sha1": "c663611e519aa8192e0a52c16664176ec1e4da6b"}
 OPS_PER_CELL = 8          # Algorithm 2 per cell: compare, add, 2 gap adds, 2 max, X-drop compare, select
 LANES_PER_SM = 128        # nominal: 4 sub-partitions x 32 lanes per clock (Blackwell SM)
 
@@ -125,6 +133,22 @@ def workload_config(b, name, pairs):
             "len_sigma": 0.5, "len_clip": [1000, 30000], "related_frac": 0.8,
             "error_rate": 0.12, "X": 100, "input": "2-bit packed",
             "l2": f"inputs larger than L2 (packed pools {packed_mb:.0f} MB), no flush", **common}
+
+
+def profiled_traffic(level: int, items: int):
+    """DRAM bytes of one launch of `level` with `items` extensions, from the
+    committed capture, or None when the kernel changed since."""
+    import hashlib
+    p = PROFILED_TRAFFIC
+    if level != p["level"]:
+        return None
+    h = hashlib.sha1()
+    for f in p["sources"]:
+        with open(os.path.join(ROOT, "paper_2002_05200_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    if h.hexdigest() != p["sha1"]:
+        return None
+    return p["bytes"] * items / p["items"]
 
 
 # ---------------------------------------------------------------- clocks
@@ -426,7 +450,9 @@ def main():
     line["roofline"] = {
         "bound": "alu", "kernel": f"window level {dom}" if dom < nl else "ring fallback",
         "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
-        "traffic": None,
+        "traffic": profiled_traffic(dom, int(last["items"][dom])),
+        "traffic_basis": "DRAM bytes per launch: ncu capture of the 24,000-pair batch scaled "
+                         "by the extensions the launch starts (null once the kernel changed)",
         "ops_per_cell": OPS_PER_CELL, "cells": dom_cells, "launch_ms": float(level_ms[dom]),
         "peak_basis": "measured: int32 max chains on all SMs (logan_intpeak op 1), the ALU-pipe "
                       "rate; of measured",
