@@ -74,6 +74,9 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the timed persistent steps (for profiler runs)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--concurrent", type=int, default=1, choices=[0, 1],
+                    help="1: the start levels of a batch run concurrently (default); "
+                         "0: level after level on one stream")
     ap.add_argument("--serving-rate", type=float, default=80.0, help="requests per second")
     ap.add_argument("--serving-requests", type=int, default=240)
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
@@ -358,6 +361,7 @@ def main():
     packed = bool(b.meta["packed2bit"])
     A, B, S, Xs = logan.batch_to_device(b, packed2bit=packed, device=f"cuda:{local}")
     ctx = logan.Context(local)
+    ctx.set_option(logan.OPT_CONCURRENT, args.concurrent)
     stream = torch.cuda.Stream()
     ws = ctx.workspace(A, B, b.n_pairs)
     out = torch.empty((b.n_pairs, 10), dtype=torch.int32, device=f"cuda:{local}")

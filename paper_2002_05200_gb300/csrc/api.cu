@@ -276,6 +276,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     ka.max_level = uint32_t(maxl);
     ka.sc = sc;
     ka.one = 1;
+    for (int k = 0; k < 16; ++k) ka.pw[k] = 1u << (31 - 2 * k);
     for (int l = 0; l < kNumLevels; ++l) {
         ka.next_level[l] = c->next_level[l];
         ka.mig_cap[l] = L.mig_cap[l];

@@ -26,6 +26,9 @@ struct KernelArgs {
     // always 1; read at run time so that "x * one + y" stays a multiply-add
     // (FMA pipe) instead of an integer add on the busier ALU pipe
     int32_t one;
+    // pw[k] = 2^(31 - 2k): multiplying a 2-bit-per-row flag word by it moves
+    // row k's flag to the sign bit (a multiply-add, FMA pipe)
+    uint32_t pw[16];
     // level an item goes to when its band outgrows level k (kNumLevels = ring)
     int8_t next_level[kNumLevels];
     // migration records written by level k (nullptr or cap 0: restart instead)

@@ -120,6 +120,9 @@ __device__ __forceinline__ uint32_t b_codes16(const KernelArgs& ka, const UState
     return rev16(load16(ka.wb, s)) >> sh;
 }
 
+// max over the G lanes of a unit: one warp reduction for a whole-warp unit,
+// else a butterfly inside each G-lane segment (a reduction with a partial
+// lane mask per unit measured ~40 % slower at G = 8)
 template <int G>
 __device__ __forceinline__ int unit_max(int v) {
     if (G == 32) return __reduce_max_sync(FULL, v);
@@ -331,30 +334,42 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
     dgc = gl == 0 ? NEGU : dgc;
     const typename Gr::Code x = u.aw ^ u.bw;
     const typename Gr::Code eq = ~(x | (x >> 1));  // bit 2k set iff row k's bases match
+    const uint32_t eq_lo = uint32_t(eq);
+    const uint32_t eq_hi = uint32_t(uint64_t(eq) >> 32);  // rows 16..31 (C = 32 only)
     // per-step constants: re-basing of d-1 and d-2 values onto T_d
     const int o1 = ka.sc.gap + u.T1 - u.T;
     const int o2 = u.T2 - u.T;
-    const int sM = ka.sc.match + o2, sMM = ka.sc.mismatch + o2;
-    // rows of this lane inside [rlo, rhi]
+    const int sMM = ka.sc.mismatch + o2;
+    const int dsub = ka.sc.mismatch - ka.sc.match;  // added back once per match (as -1 * dsub)
+    // rows of this lane inside [rlo, rhi]: bits [k0, k1) of rb
     const int i0 = u.base + gl * C;
-    const int kmin = rlo - i0, kmax = rhi - i0;
-    uint32_t rb = 0u;
-    if (C >= 8) {
-        const uint32_t lom = kmin <= 0 ? Gr::ALLC : (kmin >= C ? 0u : (Gr::ALLC << kmin) & Gr::ALLC);
-        const uint32_t him = kmax >= C - 1 ? Gr::ALLC : (kmax < 0 ? 0u : Gr::ALLC >> (C - 1 - kmax));
-        rb = lom & him;
-    }
+    const int k0 = __viaddmin_s32_relu(rlo, -i0, C);     // clamp(rlo - i0, 0, C)
+    const int k1 = __viaddmin_s32_relu(rhi, 1 - i0, C);  // clamp(rhi + 1 - i0, 0, C)
+    const uint32_t rb = __funnelshift_lc(~0u, 0u, k1) & ~__funnelshift_lc(~0u, 0u, k0);
     // Per row: v = max(up + o1, left + o1, diag + sub); the additions run as
     // multiply-adds (FMA pipe), the 3-way max is one DPX instruction, and
     // g = (d-1 value) + o1 of row k serves as "left" of row k and "up" of
-    // row k+1.
+    // row k+1.  Up to 16 rows per lane the substitution score is chosen on
+    // the FMA pipe too: the row's match flag, shifted to the sign bit by a
+    // multiply, gives y = -1 (match) or 0 as the high word of a product with
+    // 1, and sub = mismatch - y * (mismatch - match).
     const int one = ka.one;
     const int wscale = one * Gr::W;  // a run-time W keeps the key a multiply-add
     int gp = upc * one + o1;
-    int lkey = NEGU * Gr::W;
+    // the dead-row bits and the lane's largest key are collected in NCH
+    // independent chains over consecutive row blocks (short dependency chains
+    // matter when a long extension runs alone on its SM)
+    constexpr int NCH = C >= 16 ? 4 : 2, RB = C / NCH;
+    int lk[NCH];
     // dead-row bits, collected by shifting in each row's sign (dead rows hold
-    // NEGU < 0): after the loop bit C-1-k is set iff row k is dead
-    uint32_t dead = 0u;
+    // NEGU < 0): after the loop bit RB-1-(k % RB) of chain k / RB is set iff
+    // row k is dead
+    uint32_t dc[NCH];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) {
+        lk[c] = NEGU * Gr::W;
+        dc[c] = 0u;
+    }
 #pragma unroll
     for (int k = 0; k < C; k += 2) {
         int key[2];
@@ -363,28 +378,54 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
             const int kk = k + h;
             const int g = Q1[kk] * one + o1;
             const int dg = kk ? Q2[kk - 1] : dgc;
-            const bool match = (eq & (typename Gr::Code(1) << (2 * kk))) != typename Gr::Code(0);
-            const int t = dg * one + (match ? sM : sMM);
+            int t;
+            if (C <= 16) {
+                const uint32_t mw = eq_lo * ka.pw[kk];
+                const int y = __mulhi(int(mw), one);  // -1 on a match, else 0
+                t = y * dsub + (dg * one + sMM);
+            } else {
+                // the 32-row lanes are short of registers: a bit test and select
+                const bool match = ((kk < 16 ? eq_lo : eq_hi) & (1u << (2 * (kk & 15)))) != 0u;
+                t = dg * one + (match ? sMM - dsub : sMM);
+            }
             int v = __vimax3_s32(gp, g, t);
             gp = g;
-            const bool inr = (C >= 8) ? (rb & (1u << kk)) != 0u : ((kk >= kmin) & (kk <= kmax));
+            const bool inr = (rb & (1u << kk)) != 0u;
             v = (inr & (v >= 0)) ? v : NEGU;
             O[kk] = v;
             key[h] = v * wscale + (C - 1 - kk);
-            dead = __funnelshift_l(uint32_t(v), dead, 1);
+            dc[kk / RB] = __funnelshift_l(uint32_t(v), dc[kk / RB], 1);
         }
-        lkey = __vimax3_s32(lkey, key[0], key[1]);
+        lk[k / RB] = __vimax3_s32(lk[k / RB], key[0], key[1]);
     }
+    uint32_t dead = 0u;
+    int lkey = lk[0];
+#pragma unroll
+    for (int c = 0; c < NCH; ++c) dead |= dc[c] << ((NCH - 1 - c) * RB);
+#pragma unroll
+    for (int c = 1; c < NCH; ++c) lkey = max(lkey, lk[c]);
     // live rows of this lane; bit C-1-k <-> row k
     const uint32_t bits = ~dead & Gr::ALLC;
     if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
-    const uint32_t vote = __ballot_sync(FULL, bits != 0u);
-    const uint32_t uv = (G == 32) ? vote : ((vote >> (unit * G)) & ((1u << G) - 1u));
+    // the unit's first and last live window rows (W / -1 when none) and its
+    // largest key
+    int rfirst, rlast;
     const int wkey = unit_max<G>(lkey + (G - 1 - gl) * C);
-    const int fl = uv ? __ffs(uv) - 1 : 0, ll = uv ? 31 - __clz(uv) : 0;
-    const uint32_t fb = __shfl_sync(FULL, bits, unit * G + fl);
-    const uint32_t lb = __shfl_sync(FULL, bits, unit * G + ll);
-    // first live row of lane fl: highest set bit; last of lane ll: lowest
+    if (G == 32) {
+        // whole-warp unit: two more warp reductions
+        rfirst = __reduce_min_sync(FULL, bits ? gl * C + (__clz(bits) - (32 - C)) : Gr::W);
+        rlast = __reduce_max_sync(FULL, bits ? gl * C + (C - __ffs(bits)) : -1);
+    } else {
+        // first / last lane with a live row (ballot), then the row inside it
+        const uint32_t vote = __ballot_sync(FULL, bits != 0u);
+        const uint32_t uvv = (vote >> (unit * G)) & ((1u << G) - 1u);
+        const int fl = uvv ? __ffs(uvv) - 1 : 0, ll = uvv ? 31 - __clz(uvv) : 0;
+        const uint32_t fb = __shfl_sync(FULL, bits, unit * G + fl);
+        const uint32_t lb = __shfl_sync(FULL, bits, unit * G + ll);
+        rfirst = uvv ? fl * C + (__clz(fb) - (32 - C)) : Gr::W;
+        rlast = uvv ? ll * C + (C - __ffs(lb)) : -1;
+    }
+    const bool uv = rlast >= 0;
     if (run && uv) {
         // best: largest key = highest relative score, smallest row on ties
         const int umax = wkey >> Gr::LOG2W;
@@ -397,8 +438,8 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
         u.T2 = u.T1;
         u.T1 = u.T;
         u.T = u.best - u.X;
-        u.lo = u.base + fl * C + (C - 1) - (31 - __clz(fb));
-        u.hi = u.base + ll * C + (C - 1) - (__ffs(lb) - 1);
+        u.lo = u.base + rfirst;
+        u.hi = u.base + rlast;
     } else if (u.active) {
         // empty range or no live cell: the extension ends here
         u.active = false;
@@ -408,7 +449,7 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
 }
 
 template <int G, int C>
-__global__ void __launch_bounds__(128) k_group(KernelArgs ka, int level, int phase) {
+__global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) ? 5 : 7) k_group(KernelArgs ka, int level, int phase) {
     using Gr = Group<G, C>;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G, unit = lane / G;
