@@ -137,8 +137,9 @@ int logan_workspace_size(const logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   out: device logan_result_t[n_pairs].
  * Pipeline on `stream`: pack (ASCII input only) -> split + seed score ->
  * length/X binning -> phase 1: one persistent extension kernel per window
- * level over its binned items, longest first, all levels concurrently ->
- * phase 2: the escalated items, narrowest level first -> combine. With graphs enabled
+ * level (and per one-warp form, LOGAN_OPT_LONG_ITEM) over its binned items,
+ * longest first, all concurrently -> phase 2: the escalated items,
+ * narrowest level first -> combine. With graphs enabled
  * (logan_set_option) the launch sequence is captured once per shape and
  * replayed. Returns LOGAN_EINVAL for invalid scalars or pointers,
  * LOGAN_ENOMEM if ws_bytes is too small, LOGAN_ECUDA on a launch failure.
@@ -178,7 +179,7 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *     rows (wider bands give LOGAN_ERANGE for that pair).
  *   - A batch whose scratch need (logan_workspace_size with that window)
  *     exceeds LOGAN_NOALLOC_SCRATCH_BYTES is rejected with LOGAN_ENOMEM
- *     before anything is launched (about 140K pairs of 2-bit input fit).
+ *     before anything is launched (about 110K pairs of 2-bit input fit).
  *   - The first call on a device looks up the array's device address (with
  *     that device current); make that first call before any stream capture.
  *   - All no-alloc calls on a device share the array, which keeps the last
@@ -210,6 +211,7 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   LOGAN_OPT_DEVICE        (read-only) the context's device
  *   LOGAN_OPT_MIGRATION_MB  band-state migration budget (below)
  *   LOGAN_OPT_CONCURRENT    concurrent start levels (below)
+ *   LOGAN_OPT_LONG_ITEM     one-extension-per-warp forms for long items (below)
  */
 #define LOGAN_OPT_GRAPHS 1
 #define LOGAN_OPT_TIMING 2
@@ -226,6 +228,18 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                                     window level run concurrently, on streams
                                     the context creates once per caller stream;
                                     0: level after level on the caller stream */
+#define LOGAN_OPT_LONG_ITEM 10   /* extensions starting at window levels 0-3
+                                    run either several to a warp (most) or
+                                    one to a warp with the same window (fewer
+                                    instructions per anti-diagonal: what a
+                                    long extension, which a batch waits for,
+                                    or a batch too small to fill the GPU
+                                    needs).  v >= 0: one to a warp when
+                                    m + n >= v; -1: never; -2 (default):
+                                    automatic -- every item when the batch
+                                    has at most 32 items per SM, else
+                                    m + n >= 65536.  Results never depend on
+                                    it. */
 int logan_set_option(logan_ctx_t *ctx, int option, int64_t value);
 int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
 
@@ -238,8 +252,9 @@ int logan_level_info(int level, int *window_cells, int *threads_per_unit);
  * level counters to pinned host memory at its end; this function
  * synchronises on those events).
  *   level_ms[k]  device time of window level k (k < logan_num_levels()):
- *                its phase-1 launch plus its phase-2 launch, each counted
- *                only if it had entries to process; with
+ *                its phase-1 launch plus its phase-2 launch (and those of
+ *                its one-warp form), each counted only if it had entries to
+ *                process; with
  *                LOGAN_OPT_CONCURRENT the phase-1 launches overlap, so the
  *                levels' times can add up to more than total_ms;
  *                level_ms[logan_num_levels()] = the global-memory fallback;
@@ -329,8 +344,10 @@ int logan_autotune_save(const logan_ctx_t *ctx, const char *path);
  * caller's buffers (correct; with pageable buffers the scheduler thread then
  * waits for that request's copies); so is a request whose host buffers are
  * all pinned.  The server uses the context exclusively (graphs, timing and
- * concurrent levels off: each request runs on its slot's stream) until
- * logan_server_destroy, which restores those three options; do not call other functions on that context
+ * concurrent levels off: each request runs on its slot's stream;
+ * LOGAN_OPT_LONG_ITEM set per request: 65536 while at most 8 requests are
+ * in flight, else -1) until logan_server_destroy, which restores those
+ * four options; do not call other functions on that context
  * meanwhile.  The slots overlap only as far as the device's hardware work
  * queues allow: set CUDA_DEVICE_MAX_CONNECTIONS (up to 32) to at least
  * max_inflight before the process initialises CUDA, or a long extension in

@@ -20,19 +20,25 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kEvSets = 32;        // timed calls whose events are kept
-// per timed call: phase-1 start/end and phase-2 start/end of every level,
-// then pipeline start, fallback start, fallback end, pipeline end
-constexpr int EV_P1S = 0, EV_P1E = kNumLevels, EV_P2S = 2 * kNumLevels, EV_P2E = 3 * kNumLevels;
-constexpr int EV_START = 4 * kNumLevels, EV_RING_S = EV_START + 1, EV_RING_E = EV_START + 2,
-              EV_END = EV_START + 3;
-constexpr int kEvPerSet = 4 * kNumLevels + 4;
+// Launch units: the window levels (0 .. kNumLevels-1), then the one-warp
+// forms of levels 0 .. kTwinLevels-1 (unit kNumLevels + k).
+constexpr int kUnits = kNumLevels + kTwinLevels;
+inline int unit_queue(int u) { return u < kNumLevels ? u : twin_queue(u - kNumLevels); }
+inline int unit_level(int u) { return u < kNumLevels ? u : u - kNumLevels; }
 
-// Streams on which the start levels of one caller stream run concurrently.
+// per timed call: phase-1 start/end and phase-2 start/end of every unit,
+// then pipeline start, fallback start, fallback end, pipeline end
+constexpr int EV_P1S = 0, EV_P1E = kUnits, EV_P2S = 2 * kUnits, EV_P2E = 3 * kUnits;
+constexpr int EV_START = 4 * kUnits, EV_RING_S = EV_START + 1, EV_RING_E = EV_START + 2,
+              EV_END = EV_START + 3;
+constexpr int kEvPerSet = 4 * kUnits + 4;
+
+// Streams on which the start queues of one caller stream run concurrently.
 struct AuxSet {
     cudaStream_t main = nullptr;
-    cudaStream_t st[kNumLevels] = {};
+    cudaStream_t st[kUnits] = {};
     cudaEvent_t fork = nullptr;
-    cudaEvent_t join[kNumLevels] = {};
+    cudaEvent_t join[kUnits] = {};
 };
 inline size_t up(size_t v) { return (v + kAlign - 1) / kAlign * kAlign; }
 
@@ -56,6 +62,10 @@ struct logan_ctx {
     int64_t mig_mb = 64;  // migration records per level, MiB (0: restart on overflow)
     LevelTable table{};
     int blocks_per_sm[kNumLevels] = {};
+    int twin_blocks_per_sm[kTwinLevels] = {};
+    // LOGAN_OPT_LONG_ITEM: m + n from which items of levels < kTwinLevels
+    // take the one-warp form; -1 never, -2 automatic
+    int64_t long_item = -2;
     int8_t next_level[kNumLevels] = {};
     // timing: the events of the last kEvSets timed calls (ring)
     cudaEvent_t evs[kEvSets][kEvPerSet] = {};
@@ -65,7 +75,7 @@ struct logan_ctx {
         int first_level = 0;
         int max_level = 0;
         uint32_t launches = 0;
-        uint32_t p1_levels = 0;  // bit l: phase-1 events of level l recorded
+        uint32_t p1_levels = 0;  // bit u: phase-1 events of launch unit u recorded
         uint32_t p2_levels = 0;
         bool plain = false;
     } calls[kEvSets];
@@ -118,9 +128,9 @@ Layout make_layout(const logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t
     L.items = take(items * sizeof(Item));
     L.info = take(size_t(n) * sizeof(PairInfo));
     L.ext = take(items * sizeof(ExtRes));
-    L.queues = take(size_t(kNumLevels + 1) * items * sizeof(uint32_t));
+    L.queues = take(size_t(kQueues) * items * sizeof(uint32_t));
     L.counters = take(sizeof(Counters));
-    L.hist = take(sizeof(uint32_t) * kNumLevels * kBuckets);
+    L.hist = take(sizeof(uint32_t) * kQueues * kBuckets);
     L.ring_cap = 1u << c->ring_log2;
     L.ring_slots = uint32_t(std::max<size_t>(1, std::min<size_t>(size_t(c->num_sms), items)));
     L.ring = take(size_t(L.ring_slots) * 3 * L.ring_cap * sizeof(int32_t));
@@ -169,12 +179,27 @@ void default_table(LevelTable& t) {
     t.only_xclass = -1;
 }
 
-int launch_level(logan_ctx* c, int level, const KernelArgs& ka, int phase, cudaStream_t s) {
-    const int per_sm = std::max(1, c->blocks_per_sm[level]);
-    const int grid = c->num_sms * per_sm;
-    cudaError_t e = level < kWarpLevels ? launch_warp_level_persistent(level, ka, grid, phase, s)
-                                        : launch_cta_level(level, ka, grid, phase, s);
+int launch_unit(logan_ctx* c, int u, const KernelArgs& ka, int phase, cudaStream_t s) {
+    cudaError_t e;
+    if (u >= kNumLevels) {
+        const int l = u - kNumLevels;
+        const int grid = c->num_sms * std::max(1, c->twin_blocks_per_sm[l]);
+        e = launch_twin_persistent(l, ka, grid, phase, s);
+    } else {
+        const int grid = c->num_sms * std::max(1, c->blocks_per_sm[u]);
+        e = u < kWarpLevels ? launch_warp_level_persistent(u, ka, grid, phase, s)
+                            : launch_cta_level(u, ka, grid, phase, s);
+    }
     return e == cudaSuccess ? LOGAN_OK : LOGAN_ECUDA;
+}
+
+// threshold of m + n for the one-warp forms in a batch of n_items items
+uint32_t long_item_min(const logan_ctx* c, uint32_t n_items) {
+    if (c->long_item == -1) return 0xffffffffu;
+    if (c->long_item >= 0) return uint32_t(std::min<int64_t>(c->long_item, 0xfffffffe));
+    // automatic: a batch that cannot fill the GPU's warps runs every item in
+    // one-warp form; otherwise items of 64K bases and more do
+    return n_items <= uint32_t(c->num_sms) * 32u ? 0u : 65536u;
 }
 
 // The auxiliary streams of caller stream `s` (created on first use).
@@ -184,12 +209,12 @@ AuxSet* aux_for(logan_ctx* c, cudaStream_t s) {
     AuxSet a;
     a.main = s;
     bool ok = cudaEventCreateWithFlags(&a.fork, cudaEventDisableTiming) == cudaSuccess;
-    for (int l = 0; ok && l < kNumLevels; ++l) {
+    for (int l = 0; ok && l < kUnits; ++l) {
         ok = cudaStreamCreateWithFlags(&a.st[l], cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&a.join[l], cudaEventDisableTiming) == cudaSuccess;
     }
     if (!ok) {
-        for (int l = 0; l < kNumLevels; ++l) {
+        for (int l = 0; l < kUnits; ++l) {
             if (a.st[l]) cudaStreamDestroy(a.st[l]);
             if (a.join[l]) cudaEventDestroy(a.join[l]);
         }
@@ -247,6 +272,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     const int maxl = int(c->max_level);
     LevelTable tab = c->table;
     tab.max_level = maxl;
+    tab.long_min = long_item_min(c, 2u * n_pairs);
     int first = 0;
     if (e == cudaSuccess) {
         if (plain) {
@@ -299,31 +325,37 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         p1_levels |= 1u << first;
         ++launches;
     } else {
-        // phase 1: every level's binned items; the levels share no queue entry,
-        // so they run concurrently on their own streams
+        // phase 1: every queue's binned items; the queues share no entry, so
+        // they run concurrently on their own streams, the one-warp forms
+        // (long items) first
         AuxSet* ax = c->concurrent ? aux_for(c, s) : nullptr;
         if (ax && cudaEventRecord(ax->fork, s) != cudaSuccess) return LOGAN_ECUDA;
-        for (int lvl = 0; lvl <= maxl; ++lvl) {
-            cudaStream_t st = ax ? ax->st[lvl] : s;
+        for (int k = 0; k < kUnits; ++k) {
+            const int u = k < kTwinLevels ? kNumLevels + k : k - kTwinLevels;
+            if (unit_level(u) > maxl) continue;
+            cudaStream_t st = ax ? ax->st[u] : s;
             if (ax && cudaStreamWaitEvent(st, ax->fork, 0) != cudaSuccess) return LOGAN_ECUDA;
-            if (!rec(EV_P1S + lvl, st)) return LOGAN_ECUDA;
-            if (launch_level(c, lvl, ka, PHASE_INITIAL, st) != LOGAN_OK) return LOGAN_ECUDA;
-            if (!rec(EV_P1E + lvl, st)) return LOGAN_ECUDA;
-            if (ax && (cudaEventRecord(ax->join[lvl], st) != cudaSuccess ||
-                       cudaStreamWaitEvent(s, ax->join[lvl], 0) != cudaSuccess))
+            if (!rec(EV_P1S + u, st)) return LOGAN_ECUDA;
+            if (launch_unit(c, u, ka, PHASE_INITIAL, st) != LOGAN_OK) return LOGAN_ECUDA;
+            if (!rec(EV_P1E + u, st)) return LOGAN_ECUDA;
+            if (ax && (cudaEventRecord(ax->join[u], st) != cudaSuccess ||
+                       cudaStreamWaitEvent(s, ax->join[u], 0) != cudaSuccess))
                 return LOGAN_ECUDA;
-            p1_levels |= 1u << lvl;
+            p1_levels |= 1u << u;
             ++launches;
         }
     }
-    // phase 2: escalated items, narrowest level first (each level can only
-    // receive items from narrower ones)
+    // phase 2: escalated items, narrowest level first (a queue only receives
+    // items from narrower levels); a level's one-warp form after the level
     for (int lvl = (plain ? first + 1 : 0); lvl <= maxl; ++lvl) {
-        if (!rec(EV_P2S + lvl, s)) return LOGAN_ECUDA;
-        if (launch_level(c, lvl, ka, PHASE_ESCALATED, s) != LOGAN_OK) return LOGAN_ECUDA;
-        if (!rec(EV_P2E + lvl, s)) return LOGAN_ECUDA;
-        p2_levels |= 1u << lvl;
-        ++launches;
+        for (int u : {lvl, lvl < kTwinLevels && !plain ? kNumLevels + lvl : -1}) {
+            if (u < 0) continue;
+            if (!rec(EV_P2S + u, s)) return LOGAN_ECUDA;
+            if (launch_unit(c, u, ka, PHASE_ESCALATED, s) != LOGAN_OK) return LOGAN_ECUDA;
+            if (!rec(EV_P2E + u, s)) return LOGAN_ECUDA;
+            p2_levels |= 1u << u;
+            ++launches;
+        }
     }
     // ring fallback: one resident block per ring slot
     if (!rec(EV_RING_S, s)) return LOGAN_ECUDA;
@@ -377,7 +409,7 @@ int extend_common(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         uint64_t(uintptr_t(seeds)), uint64_t(uintptr_t(out)), uint64_t(uintptr_t(ws)),
         uint64_t(uintptr_t(stream)), uint64_t(c->force_level), uint64_t(c->max_level),
         uint64_t(c->ring_log2), uint64_t(c->plain_level), uint64_t(c->mig_mb),
-        uint64_t(c->concurrent)};
+        uint64_t(c->concurrent), uint64_t(c->long_item)};
     for (const logan_seqs_t* p : {A, B}) {
         key.push_back(uint64_t(uintptr_t(p->bases)));
         key.push_back(uint64_t(uintptr_t(p->offsets)));
@@ -499,6 +531,7 @@ int logan_ctx_create(logan_ctx_t** out, int device, const char* autotune_json) {
     for (int l = 0; l < kNumLevels; ++l) c->next_level[l] = int8_t(l + 1);
     for (int l = 0; l < kNumLevels; ++l)
         c->blocks_per_sm[l] = l < kWarpLevels ? warp_level_blocks_per_sm(l) : cta_level_blocks_per_sm(l);
+    for (int l = 0; l < kTwinLevels; ++l) c->twin_blocks_per_sm[l] = twin_blocks_per_sm(l);
     for (auto& set : c->evs)
         for (auto& ev : set)
             if (cudaEventCreate(&ev) != cudaSuccess) {
@@ -527,7 +560,7 @@ void logan_ctx_destroy(logan_ctx_t* c) {
     for (auto& ge : c->graphs)
         if (ge.exec) cudaGraphExecDestroy(ge.exec);
     for (auto& a : c->aux) {
-        for (int l = 0; l < kNumLevels; ++l) {
+        for (int l = 0; l < kUnits; ++l) {
             if (a.st[l]) {
                 cudaStreamSynchronize(a.st[l]);
                 cudaStreamDestroy(a.st[l]);
@@ -592,6 +625,10 @@ int logan_set_option(logan_ctx_t* c, int option, int64_t v) {
             c->mig_mb = v;
             return LOGAN_OK;
         case LOGAN_OPT_CONCURRENT: c->concurrent = v ? 1 : 0; return LOGAN_OK;
+        case LOGAN_OPT_LONG_ITEM:
+            if (v < -2) return LOGAN_EINVAL;
+            c->long_item = v;
+            return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }
@@ -608,6 +645,7 @@ int logan_get_option(const logan_ctx_t* c, int option, int64_t* v) {
         case LOGAN_OPT_DEVICE: *v = c->device; return LOGAN_OK;
         case LOGAN_OPT_MIGRATION_MB: *v = c->mig_mb; return LOGAN_OK;
         case LOGAN_OPT_CONCURRENT: *v = c->concurrent; return LOGAN_OK;
+        case LOGAN_OPT_LONG_ITEM: *v = c->long_item; return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }
@@ -633,16 +671,18 @@ int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
     std::memset(st, 0, sizeof(*st));
     const Counters& h = c->hcounters[call % kEvSets];
     // a launch counts only if it had entries to process: an empty launch's
-    // span is mostly its wait for room on the SMs
-    for (int l = 0; l < kNumLevels; ++l) {
+    // span is mostly its wait for room on the SMs; a one-warp form's time
+    // and items count for its level
+    for (int u = 0; u < kUnits; ++u) {
+        const int q = unit_queue(u), l = unit_level(u);
         float ms = 0.f;
-        if (((ci.p1_levels >> l) & 1u) && (h.started[l] > 0 || ci.plain)) {
-            if (cudaEventElapsedTime(&ms, ev[EV_P1S + l], ev[EV_P1E + l]) != cudaSuccess)
+        if (((ci.p1_levels >> u) & 1u) && (h.started[q] > 0 || ci.plain)) {
+            if (cudaEventElapsedTime(&ms, ev[EV_P1S + u], ev[EV_P1E + u]) != cudaSuccess)
                 return LOGAN_ECUDA;
             st->level_ms[l] += ms;
         }
-        if (((ci.p2_levels >> l) & 1u) && h.tail[l] > h.started[l]) {
-            if (cudaEventElapsedTime(&ms, ev[EV_P2S + l], ev[EV_P2E + l]) != cudaSuccess)
+        if (((ci.p2_levels >> u) & 1u) && h.tail[q] > h.started[q]) {
+            if (cudaEventElapsedTime(&ms, ev[EV_P2S + u], ev[EV_P2E + u]) != cudaSuccess)
                 return LOGAN_ECUDA;
             st->level_ms[l] += ms;
         }
@@ -652,7 +692,7 @@ int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
     if (cudaEventElapsedTime(&st->total_ms, ev[EV_START], ev[EV_END]) != cudaSuccess)
         return LOGAN_ECUDA;
     for (int l = 0; l <= kNumLevels; ++l) {
-        st->items[l] = h.tail[l];
+        st->items[l] = h.tail[l] + (l < kTwinLevels ? h.tail[twin_queue(l)] : 0u);
         st->cells[l] = h.cells[l];
     }
     st->launches = ci.launches;

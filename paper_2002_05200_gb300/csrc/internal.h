@@ -54,11 +54,22 @@ __device__ __forceinline__ int escalate(const KernelArgs& ka, int level) {
     return nl <= int(ka.max_level) ? nl : kNumLevels;
 }
 
+// queue an item outgrowing `level` goes to: a one-warp form's items stay in
+// one-warp forms while the next level has one
+__device__ __forceinline__ int escalate_queue(const KernelArgs& ka, int level, bool twin) {
+    const int nl = escalate(ka, level);
+    return (twin && nl < kTwinLevels) ? twin_queue(nl) : nl;
+}
+
 // extension kernels (xdrop_group.cu / xdrop_cta.cu / xdrop_ring.cu)
 cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid, int phase,
                                          cudaStream_t s);
 cudaError_t launch_warp_level_plain(int level, const KernelArgs& ka, cudaStream_t s);
 int warp_level_blocks_per_sm(int level);
+// level k's one-warp form (k < kTwinLevels), persistent over twin_queue(k)
+cudaError_t launch_twin_persistent(int level, const KernelArgs& ka, int grid, int phase,
+                                   cudaStream_t s);
+int twin_blocks_per_sm(int level);
 cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int phase, cudaStream_t s);
 int cta_level_blocks_per_sm(int level);
 cudaError_t launch_ring(const KernelArgs& ka, int grid, cudaStream_t s);
@@ -87,6 +98,9 @@ struct LevelTable {
     int8_t lv[8];
     int max_level;
     int only_xclass;
+    // items with m + n >= long_min that start below level kTwinLevels go to
+    // that level's one-warp form (0xffffffff: none)
+    uint32_t long_min;
 };
 cudaError_t launch_bin(const Item* items, uint32_t n_items, LevelTable table, int force_level, uint32_t* hist, uint32_t* queues, uint32_t qcap,
                        Counters* counters, cudaStream_t s);

@@ -79,16 +79,29 @@ __host__ __device__ constexpr int level_threads(int k) {
 }
 __host__ __device__ constexpr int level_window(int k) { return level_cells(k) * level_threads(k); }
 
+// One-warp forms.  Levels 0..kTwinLevels-1 put several extensions in a warp,
+// which keeps the lanes busy but makes every anti-diagonal step of one
+// extension cost a whole warp's instructions.  A long item (the one a
+// batch waits for) or an item of a batch too small to fill the GPU runs
+// instead in the level's one-warp form: the same window, G = 32 lanes of
+// window/32 rows each, so a step is about half the instructions and its
+// reductions are single warp reductions.
+constexpr int kTwinLevels = 4;
+__host__ __device__ constexpr int twin_cells(int k) { return level_window(k) / 32; }
+
 // Work queues: queue k (k <= kNumLevels) holds the items that level k runs,
-// first those binned to it (longest first), then those escalated from k-1.
+// first those binned to it (longest first), then those escalated from k-1;
+// queue twin_queue(k) the same for level k's one-warp form.
+constexpr int kQueues = kNumLevels + 1 + kTwinLevels;
+__host__ __device__ constexpr int twin_queue(int level) { return kNumLevels + 1 + level; }
 struct Counters {
-    unsigned int tail[kNumLevels + 1];
-    unsigned int head[kNumLevels + 1];
-    unsigned int started[kNumLevels + 1];   // items that began at this level (binning)
+    unsigned int tail[kQueues];
+    unsigned int head[kQueues];
+    unsigned int started[kQueues];             // items that began in this queue (binning)
     unsigned int pad;
-    unsigned long long cells[kNumLevels + 1];  // cells computed by each level
+    unsigned long long cells[kNumLevels + 1];  // cells computed by each level (both forms)
     unsigned int mig_used[kNumLevels];         // migration records written per level
-    unsigned int head2[kNumLevels + 1];        // pop cursor of the escalated entries
+    unsigned int head2[kQueues];               // pop cursor of the escalated entries
 };
 
 // Which entries of a level's queue a launch processes: the binned (initial)
@@ -98,14 +111,26 @@ constexpr int PHASE_INITIAL = 0;
 constexpr int PHASE_ESCALATED = 1;
 constexpr int PHASE_PLAIN = 2;
 
-// Next queue slot of `level` for this phase, or ~0u when the range is used up.
-__device__ __forceinline__ unsigned int pop_slot(Counters* c, int level, int phase) {
+// n consecutive slots of queue `q` for this phase: returns the first; those
+// at or past *limit are used up.
+__device__ __forceinline__ unsigned int pop_slots(Counters* c, int q, int phase, unsigned int n,
+                                                  unsigned int* limit) {
     if (phase == PHASE_INITIAL) {
-        const unsigned int s = atomicAdd(&c->head[level], 1u);
-        return s < c->started[level] ? s : ~0u;
+        *limit = c->started[q];
+        return atomicAdd(&c->head[q], n);
     }
-    const unsigned int s = c->started[level] + atomicAdd(&c->head2[level], 1u);
-    return s < c->tail[level] ? s : ~0u;
+    *limit = c->tail[q];
+    return c->started[q] + atomicAdd(&c->head2[q], n);
+}
+
+// Next slot of queue `q` for this phase, or ~0u when the range is used up.
+__device__ __forceinline__ unsigned int pop_slot(Counters* c, int q, int phase) {
+    if (phase == PHASE_INITIAL) {
+        const unsigned int s = atomicAdd(&c->head[q], 1u);
+        return s < c->started[q] ? s : ~0u;
+    }
+    const unsigned int s = c->started[q] + atomicAdd(&c->head2[q], 1u);
+    return s < c->tail[q] ? s : ~0u;
 }
 
 // Band-state migration.  A unit whose band outgrows its window writes its

@@ -142,29 +142,38 @@ __device__ __forceinline__ int item_level(const Item& it, LevelTable table, int 
     return min(l, maxl);
 }
 
+// queue of an item: its starting level, or that level's one-warp form for a
+// long item; -1 when the X-class filter leaves it out
+__device__ __forceinline__ int item_queue(const Item& it, LevelTable table, int force, int maxl) {
+    const int l = item_level(it, table, force, maxl);
+    if (l >= 0 && l < kTwinLevels && uint64_t(it.m) + it.n >= table.long_min) return twin_queue(l);
+    return l;
+}
+
 __global__ void k_bin_hist(const Item* __restrict__ items, uint32_t n, LevelTable table,
                            int force, int maxl, uint32_t* __restrict__ hist) {
-    __shared__ uint32_t h[kNumLevels * kBuckets];
-    for (int t = threadIdx.x; t < kNumLevels * kBuckets; t += blockDim.x) h[t] = 0u;
+    __shared__ uint32_t h[kQueues * kBuckets];
+    for (int t = threadIdx.x; t < kQueues * kBuckets; t += blockDim.x) h[t] = 0u;
     __syncthreads();
     for (uint32_t i = blockIdx.x * blockDim.x + threadIdx.x; i < n; i += gridDim.x * blockDim.x) {
         const Item it = items[i];
         if (it.flags & ITEM_SKIP) continue;
-        const int l = item_level(it, table, force, maxl);
-        if (l < 0) continue;
-        atomicAdd(&h[l * kBuckets + (kBuckets - 1 - work_bucket(it.m, it.n))], 1u);
+        const int q = item_queue(it, table, force, maxl);
+        if (q < 0) continue;
+        atomicAdd(&h[q * kBuckets + (kBuckets - 1 - work_bucket(it.m, it.n))], 1u);
     }
     __syncthreads();
-    for (int t = threadIdx.x; t < kNumLevels * kBuckets; t += blockDim.x)
+    for (int t = threadIdx.x; t < kQueues * kBuckets; t += blockDim.x)
         if (h[t]) atomicAdd(&hist[t], h[t]);
 }
 
-// one block of kBuckets threads: per level exclusive scan of the bucket
-// counts (longest bucket first) -> cursors; queue sizes -> counters
+// one block of kBuckets threads: per queue exclusive scan of the bucket
+// counts (longest bucket first) -> cursors; queue sizes -> counters (the
+// fallback ring's queue gets no binned items)
 __global__ void k_bin_scan(uint32_t* __restrict__ hist, Counters* __restrict__ c) {
     __shared__ uint32_t s[kBuckets];
     const int t = threadIdx.x;
-    for (int l = 0; l < kNumLevels; ++l) {
+    for (int l = 0; l < kQueues; ++l) {
         const uint32_t v = hist[l * kBuckets + t];
         s[t] = v;
         __syncthreads();
@@ -181,16 +190,12 @@ __global__ void k_bin_scan(uint32_t* __restrict__ hist, Counters* __restrict__ c
         }
         __syncthreads();
     }
-    if (t <= kNumLevels) {
+    if (t < kQueues) {
         c->head[t] = 0u;
         c->head2[t] = 0u;
-        c->cells[t] = 0ull;
     }
+    if (t <= kNumLevels) c->cells[t] = 0ull;
     if (t < kNumLevels) c->mig_used[t] = 0u;
-    if (t == 0) {
-        c->tail[kNumLevels] = 0u;
-        c->started[kNumLevels] = 0u;
-    }
 }
 
 __global__ void k_bin_scatter(const Item* __restrict__ items, uint32_t n, LevelTable table,
@@ -200,21 +205,21 @@ __global__ void k_bin_scatter(const Item* __restrict__ items, uint32_t n, LevelT
     if (i >= n) return;
     const Item it = items[i];
     if (it.flags & ITEM_SKIP) return;
-    const int l = item_level(it, table, force, maxl);
-    if (l < 0) return;
-    const uint32_t pos = atomicAdd(&cursor[l * kBuckets + (kBuckets - 1 - work_bucket(it.m, it.n))], 1u);
-    queues[size_t(l) * qcap + pos] = i;
+    const int q = item_queue(it, table, force, maxl);
+    if (q < 0) return;
+    const uint32_t pos = atomicAdd(&cursor[q * kBuckets + (kBuckets - 1 - work_bucket(it.m, it.n))], 1u);
+    queues[size_t(q) * qcap + pos] = i;
 }
 
 __global__ void k_reset_counters(Counters* c, uint32_t first_items, int first_level) {
     const int t = threadIdx.x;
-    if (t <= kNumLevels) {
+    if (t < kQueues) {
         c->head[t] = 0u;
         c->head2[t] = 0u;
         c->tail[t] = 0u;
         c->started[t] = 0u;  // the plain kernel takes items directly
-        c->cells[t] = 0ull;
     }
+    if (t <= kNumLevels) c->cells[t] = 0ull;
     (void)first_items;
     (void)first_level;
     if (t < kNumLevels) c->mig_used[t] = 0u;
@@ -284,7 +289,7 @@ cudaError_t launch_split(const PoolDev& A, const PoolDev& B, const void* seeds, 
 cudaError_t launch_bin(const Item* items, uint32_t n_items, LevelTable table, int force_level,
                        uint32_t* hist, uint32_t* queues, uint32_t qcap, Counters* counters,
                        cudaStream_t s) {
-    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kNumLevels * kBuckets, s);
+    cudaError_t e = cudaMemsetAsync(hist, 0, sizeof(uint32_t) * kQueues * kBuckets, s);
     if (e != cudaSuccess) return e;
     const int maxl = table.max_level;
     if (n_items) {

@@ -26,6 +26,7 @@
 // host bytes exceed the whole staging arena, is copied directly (for the
 // latter, with pageable buffers, the scheduler waits for its copies).
 #include <algorithm>
+#include <atomic>
 #include <chrono>
 #include <condition_variable>
 #include <cstring>
@@ -186,7 +187,9 @@ struct logan_server {
     bool stop = false;
     std::thread th;
     uint64_t n_done = 0, n_failed = 0, n_cancelled = 0;
-    int64_t saved_opts[3] = {0, 0, 1};  // graphs, timing, concurrent: restored at destroy
+    // graphs, timing, concurrent, long item: restored at destroy
+    int64_t saved_opts[4] = {0, 0, 1, -2};
+    std::atomic<int> running{0};  // admitted requests not yet completed
 };
 
 namespace {
@@ -214,6 +217,7 @@ void CUDART_CB on_done(void* p) {
             s->arena.release(q.off, q.bytes);
             if (q.hbytes) s->harena.release(q.hoff, q.hbytes);
             s->slots[q.slot].ticket = 0;
+            s->running.fetch_sub(1);
             s->n_done++;
         }
     }
@@ -281,6 +285,10 @@ int launch(logan_server* s, uint64_t ticket, Req& q) {
     if (e == cudaSuccess) e = h2d(seeds, r.seeds, size_t(r.n_pairs) * sizeof(logan_seed_t));
     if (e == cudaSuccess && xs) e = h2d(xs, r.X_per_pair, size_t(r.n_pairs) * 4);
     if (e != cudaSuccess) return LOGAN_ECUDA;
+    // with the GPU nearly idle, long extensions run one to a warp (shorter
+    // latency); with several requests in flight every extension runs in the
+    // several-to-a-warp forms (more extensions per instruction)
+    logan_set_option(s->ctx, LOGAN_OPT_LONG_ITEM, s->running.load() <= 8 ? 65536 : -1);
     int rc = logan_extend_batch(s->ctx, &dA, &dB, reinterpret_cast<const logan_seed_t*>(seeds),
                                 r.n_pairs, r.match, r.mismatch, r.gap, r.X,
                                 reinterpret_cast<const int32_t*>(xs), ws, q.ws_bytes,
@@ -331,6 +339,7 @@ void scheduler(logan_server* s) {
             q.off = off;
             q.t_admit = now_s();
             s->slots[slot].ticket = t;
+            s->running.fetch_add(1);
             lk.unlock();
             const int rc = launch(s, t, q);  // q stays valid: entries are erased only when done
             lk.lock();
@@ -346,6 +355,7 @@ void scheduler(logan_server* s) {
                 s->arena.release(q.off, q.bytes);
                 if (q.hbytes) s->harena.release(q.hoff, q.hbytes);
                 s->slots[slot].ticket = 0;
+                s->running.fetch_sub(1);
                 s->n_failed++;
                 s->done_cv.notify_all();
             }
@@ -408,9 +418,15 @@ int logan_server_create(logan_ctx_t* ctx, size_t budget_bytes, int max_inflight,
     logan_get_option(ctx, LOGAN_OPT_GRAPHS, &s->saved_opts[0]);
     logan_get_option(ctx, LOGAN_OPT_TIMING, &s->saved_opts[1]);
     logan_get_option(ctx, LOGAN_OPT_CONCURRENT, &s->saved_opts[2]);
+    logan_get_option(ctx, LOGAN_OPT_LONG_ITEM, &s->saved_opts[3]);
     logan_set_option(ctx, LOGAN_OPT_GRAPHS, 0);
     logan_set_option(ctx, LOGAN_OPT_TIMING, 0);
     logan_set_option(ctx, LOGAN_OPT_CONCURRENT, 0);
+    // a request is small next to the GPU but shares it with the other
+    // slots: the scheduler picks LOGAN_OPT_LONG_ITEM per request from the
+    // load (the automatic rule would put every item of a small request in
+    // the one-extension-per-warp forms)
+    logan_set_option(ctx, LOGAN_OPT_LONG_ITEM, 65536);
     s->th = std::thread(scheduler, s);
     *out = s;
     return LOGAN_OK;
@@ -546,6 +562,7 @@ int logan_server_destroy(logan_server_t* s) {
     logan_set_option(s->ctx, LOGAN_OPT_GRAPHS, s->saved_opts[0]);
     logan_set_option(s->ctx, LOGAN_OPT_TIMING, s->saved_opts[1]);
     logan_set_option(s->ctx, LOGAN_OPT_CONCURRENT, s->saved_opts[2]);
+    logan_set_option(s->ctx, LOGAN_OPT_LONG_ITEM, s->saved_opts[3]);
     delete s;
     return LOGAN_OK;
 }

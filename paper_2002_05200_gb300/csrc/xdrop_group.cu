@@ -125,10 +125,13 @@ __device__ __forceinline__ uint32_t b_codes16(const KernelArgs& ka, const UState
 // lane mask per unit measured ~40 % slower at G = 8)
 template <int G>
 __device__ __forceinline__ int unit_max(int v) {
-    if (G == 32) return __reduce_max_sync(FULL, v);
+    if constexpr (G == 32) {
+        return __reduce_max_sync(FULL, v);
+    } else {
 #pragma unroll
-    for (int o = G / 2; o >= 1; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o, G));
-    return v;
+        for (int o = G / 2; o >= 1; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o, G));
+        return v;
+    }
 }
 
 template <int G, int C>
@@ -208,13 +211,13 @@ __device__ __forceinline__ void unit_init(const KernelArgs& ka, UState<C>& u, ui
 // Result or escalation of a finished unit (its leader lane writes).
 template <int C>
 __device__ __forceinline__ void unit_finish(const KernelArgs& ka, const UState<C>& u, int level,
-                                            int gl) {
+                                            int gl, bool twin) {
     if (gl != 0) return;
     if (u.overflow) {
         if (u.migrated) atomicAdd(&ka.counters->cells[level], u.cells - u.cells0);
-        const int nl = escalate(ka, level);
-        const unsigned int t = atomicAdd(&ka.counters->tail[nl], 1u);
-        ka.queues[size_t(nl) * ka.qcap + t] = u.item;
+        const int nq = escalate_queue(ka, level, twin);
+        const unsigned int t = atomicAdd(&ka.counters->tail[nq], 1u);
+        ka.queues[size_t(nq) * ka.qcap + t] = u.item;
     } else {
         ExtRes r;
         r.best = u.best;
@@ -359,7 +362,7 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
     // the dead-row bits and the lane's largest key are collected in NCH
     // independent chains over consecutive row blocks (short dependency chains
     // matter when a long extension runs alone on its SM)
-    constexpr int NCH = C >= 16 ? 4 : 2, RB = C / NCH;
+    constexpr int NCH = C >= 16 ? 4 : C >= 2 ? 2 : 1, RB = C / NCH;
     int lk[NCH];
     // dead-row bits, collected by shifting in each row's sign (dead rows hold
     // NEGU < 0): after the loop bit RB-1-(k % RB) of chain k / RB is set iff
@@ -372,10 +375,11 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
     }
 #pragma unroll
     for (int k = 0; k < C; k += 2) {
-        int key[2];
+        int key[2] = {NEGU * Gr::W, NEGU * Gr::W};
 #pragma unroll
         for (int h = 0; h < 2; ++h) {
             const int kk = k + h;
+            if (kk >= C) break;  // C = 1
             const int g = Q1[kk] * one + o1;
             const int dg = kk ? Q2[kk - 1] : dgc;
             int t;
@@ -411,7 +415,7 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
     // largest key
     int rfirst, rlast;
     const int wkey = unit_max<G>(lkey + (G - 1 - gl) * C);
-    if (G == 32) {
+    if constexpr (G == 32) {
         // whole-warp unit: two more warp reductions
         rfirst = __reduce_min_sync(FULL, bits ? gl * C + (__clz(bits) - (32 - C)) : Gr::W);
         rlast = __reduce_max_sync(FULL, bits ? gl * C + (C - __ffs(bits)) : -1);
@@ -449,13 +453,14 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
 }
 
 template <int G, int C>
-__global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) ? 5 : 7) k_group(KernelArgs ka, int level, int phase) {
+__global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) ? 5 : 7)
+    k_group(KernelArgs ka, int level, int queue, int phase) {
     using Gr = Group<G, C>;
     const int lane = threadIdx.x & 31;
     const int gl = lane % G, unit = lane / G;
-    const unsigned int umask = (G == 32) ? FULL : (((1u << G) - 1u) << (unit * G));
     const bool plain = phase == PHASE_PLAIN;
-    const uint32_t* q = ka.queues + size_t(level) * ka.qcap;
+    const bool twin = queue != level;  // level's one-warp form
+    const uint32_t* q = ka.queues + size_t(queue) * ka.qcap;
     // plain form: one fixed item per unit, in input order
     const uint32_t plain_id =
         (blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * Gr::U + unit;
@@ -488,22 +493,34 @@ __global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) 
     for (;;) {
         if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
             if (u.done) {
-                unit_finish(ka, u, level, gl);
+                unit_finish(ka, u, level, gl, twin);
                 u.done = false;
             }
-            if (!u.active && !exhausted) {
-                // this unit takes its next item (lanes of the unit only)
-                uint32_t id = 0xffffffffu;
-                if (plain) {
-                    if (fresh && plain_id < ka.n_items && !(ka.items[plain_id].flags & ITEM_SKIP))
-                        id = plain_id;
-                    fresh = false;
-                } else {
-                    unsigned int slot = 0u;
-                    if (gl == 0) slot = pop_slot(ka.counters, level, phase);
-                    slot = __shfl_sync(umask, slot, unit * G);
-                    if (slot != ~0u) id = q[slot];
+            const bool need = !u.active && !exhausted;  // the same in all lanes of a unit
+            uint32_t id = 0xffffffffu;
+            if (plain) {
+                if (need && fresh && plain_id < ka.n_items &&
+                    !(ka.items[plain_id].flags & ITEM_SKIP))
+                    id = plain_id;
+                if (need) fresh = false;
+            } else {
+                // one pop per warp for all of its idle units, so that a batch
+                // with fewer items than unit slots fills whole warps (a warp
+                // costs the same whether its units are busy or idle)
+                const uint32_t want = __ballot_sync(FULL, need && gl == 0);
+                if (want) {
+                    const int leader = __ffs(want) - 1;
+                    unsigned int first = 0u, limit = 0u;
+                    if (lane == leader)
+                        first = pop_slots(ka.counters, queue, phase, unsigned(__popc(want)), &limit);
+                    first = __shfl_sync(FULL, first, leader);
+                    limit = __shfl_sync(FULL, limit, leader);
+                    const unsigned int slot =
+                        first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
+                    if (need && slot < limit) id = q[slot];
                 }
+            }
+            if (need) {
                 if (id != 0xffffffffu) unit_init<G, C>(ka, u, id, gl, P0, P1);
                 else exhausted = true;
             }
@@ -522,12 +539,29 @@ __global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) 
 // level -> (G, C)
 #define LOGAN_GROUP_LEVELS(X) \
     X(0, 8, 4) X(1, 8, 8) X(2, 8, 16) X(3, 16, 16) X(4, 32, 16) X(5, 32, 32)
+// level -> (32, window / 32): the one-warp forms
+#define LOGAN_TWIN_LEVELS(X) X(0, 32, 1) X(1, 32, 2) X(2, 32, 4) X(3, 32, 8)
 
 cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int grid, int phase,
                                          cudaStream_t s) {
     switch (level) {
-#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, phase); break;
+#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, level, phase); break;
         LOGAN_GROUP_LEVELS(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+cudaError_t launch_twin_persistent(int level, const KernelArgs& ka, int grid, int phase,
+                                   cudaStream_t s) {
+    switch (level) {
+#define CASE(L, G, C)                                                                           \
+    case L:                                                                                     \
+        static_assert(G * C == level_window(L), "a one-warp form keeps its level's window");  \
+        k_group<G, C><<<grid, 128, 0, s>>>(ka, level, twin_queue(level), phase);               \
+        break;
+        LOGAN_TWIN_LEVELS(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
     }
@@ -545,7 +579,8 @@ cudaError_t launch_warp_level_plain(int level, const KernelArgs& ka, cudaStream_
     const unsigned int grid = (ka.n_items + units_per_block - 1) / units_per_block;
     if (grid == 0) return cudaSuccess;
     switch (level) {
-#define CASE(L, G, C) case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, PHASE_PLAIN); break;
+#define CASE(L, G, C) \
+    case L: k_group<G, C><<<grid, 128, 0, s>>>(ka, level, level, PHASE_PLAIN); break;
         LOGAN_GROUP_LEVELS(CASE)
 #undef CASE
         default: return cudaErrorInvalidValue;
@@ -560,6 +595,19 @@ int warp_level_blocks_per_sm(int level) {
 #define CASE(L, G, C) \
     case L: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_group<G, C>, 128, 0); break;
         LOGAN_GROUP_LEVELS(CASE)
+#undef CASE
+        default: break;
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+int twin_blocks_per_sm(int level) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (level) {
+#define CASE(L, G, C) \
+    case L: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_group<G, C>, 128, 0); break;
+        LOGAN_TWIN_LEVELS(CASE)
 #undef CASE
         default: break;
     }

@@ -21,7 +21,7 @@ OK = 0
 EINVAL, ENOMEM, EAGAIN, ECUDA, ETIMEOUT, ECANCELED, ERANGE, ENOTFOUND = \
     -22, -12, -11, -5, -110, -125, -34, -2
 OPT_GRAPHS, OPT_TIMING, OPT_FORCE_LEVEL, OPT_MAX_LEVEL, OPT_RING_CAP, OPT_PLAIN_LEVEL = 1, 2, 3, 4, 5, 6
-OPT_DEVICE, OPT_MIGRATION_MB, OPT_CONCURRENT = 7, 8, 9
+OPT_DEVICE, OPT_MIGRATION_MB, OPT_CONCURRENT, OPT_LONG_ITEM = 7, 8, 9, 10
 X_CLASSES = 8
 
 RESULT_DTYPE = np.dtype([("score", "<i4"), ("left", "<i4"), ("right", "<i4"), ("status", "<i4"),

@@ -25,7 +25,7 @@ def _reset(ctx):
     for opt, v in ((logan.OPT_FORCE_LEVEL, -1), (logan.OPT_MAX_LEVEL, logan.num_levels() - 1),
                    (logan.OPT_GRAPHS, 0), (logan.OPT_RING_CAP, 16), (logan.OPT_PLAIN_LEVEL, 1),
                    (logan.OPT_TIMING, 0), (logan.OPT_MIGRATION_MB, 64),
-                   (logan.OPT_CONCURRENT, 1)):
+                   (logan.OPT_CONCURRENT, 1), (logan.OPT_LONG_ITEM, -2)):
         ctx.set_option(opt, v)
     yield
 
@@ -61,11 +61,14 @@ def test_tiny_edge_cases(ctx, seed):
     assert_same(run_gpu(ctx, b, packed2bit=True, plain=True), ref, "plain")
 
 
+@pytest.mark.parametrize("long_item", [-1, 0])
 @pytest.mark.parametrize("level", range(8))
-def test_every_window_level(ctx, level):
-    # each level started directly; narrower bands stay, wider ones escalate
+def test_every_window_level(ctx, level, long_item):
+    # each level started directly; narrower bands stay, wider ones escalate;
+    # levels 0-3 in their several-to-a-warp form (-1) and one-to-a-warp form (0)
     b = synth.uneven_batch(n_pairs=120, max_len=12_000, seed=21)
     ref = run_oracle(b)
+    ctx.set_option(logan.OPT_LONG_ITEM, long_item)
     ctx.set_option(logan.OPT_FORCE_LEVEL, level)
     assert_same(run_gpu(ctx, b, packed2bit=True), ref, f"level {level}")
     ctx.set_option(logan.OPT_PLAIN_LEVEL, level)
@@ -256,3 +259,26 @@ def test_concurrent_and_serial_levels_agree(ctx, graphs):
             out = ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, stream=stream)
         stream.synchronize()
         assert_same(logan.results_to_numpy(out), ref, f"concurrent={conc} graphs={graphs}")
+
+
+@pytest.mark.parametrize("long_item", [-2, -1, 0, 3000, 1 << 20])
+def test_long_item_forms(ctx, long_item):
+    # which extensions run one to a warp changes only the speed: mixed
+    # lengths and X, with and without band-state records, graphs replayed
+    b = synth.uneven_batch(n_pairs=300, max_len=30_000, seed=61)
+    ref = run_oracle(b)
+    ctx.set_option(logan.OPT_LONG_ITEM, long_item)
+    assert ctx.get_option(logan.OPT_LONG_ITEM) == long_item
+    ctx.set_option(logan.OPT_TIMING, 1)
+    g = run_gpu(ctx, b, packed2bit=True)
+    assert_same(g, ref, f"long item {long_item}")
+    st = ctx.last_stats()
+    assert sum(st["cells"]) == int(g["cells"].sum())
+    assert sum(st["items"]) >= np.count_nonzero(b.lenA > 0)
+    ctx.set_option(logan.OPT_TIMING, 0)
+    ctx.set_option(logan.OPT_MIGRATION_MB, 0)
+    assert_same(run_gpu(ctx, b, packed2bit=True), ref, f"long item {long_item}, restarts")
+    ctx.set_option(logan.OPT_MIGRATION_MB, 64)
+    assert_same(run_gpu(ctx, b, packed2bit=True, graphs=True), ref, f"long item {long_item}, graph")
+    with pytest.raises(logan.LoganError):
+        ctx.set_option(logan.OPT_LONG_ITEM, -3)

@@ -133,6 +133,7 @@ def test_pageable_and_pinned_requests(ctx, pin):
     srv = logan.Server(ctx, budget_bytes=1 << 30, max_inflight=4)
     try:
         assert ctx.get_option(logan.OPT_CONCURRENT) == 0
+        assert ctx.get_option(logan.OPT_LONG_ITEM) in (65536, -1)
         tickets = [srv.submit(h) for h in hosts]
         for t in tickets:
             st, _ = srv.wait(t, timeout_ms=120_000)
@@ -140,5 +141,6 @@ def test_pageable_and_pinned_requests(ctx, pin):
     finally:
         srv.close()
     assert ctx.get_option(logan.OPT_CONCURRENT) == 1
+    assert ctx.get_option(logan.OPT_LONG_ITEM) == -2
     for h, a in zip(hosts, alone):
         np.testing.assert_array_equal(h.result_array(), a)
