@@ -137,7 +137,7 @@ int logan_workspace_size(const logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   out: device logan_result_t[n_pairs].
  * Pipeline on `stream`: pack (ASCII input only) -> split + seed score ->
  * length/X binning -> phase 1: one persistent extension kernel per window
- * level (and per one-warp form, LOGAN_OPT_LONG_ITEM) over its binned items,
+ * level (and per latency form, LOGAN_OPT_LONG_ITEM) over its binned items,
  * longest first, all concurrently -> phase 2: the escalated items,
  * narrowest level first -> combine. With graphs enabled
  * (logan_set_option) the launch sequence is captured once per shape and
@@ -211,7 +211,7 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   LOGAN_OPT_DEVICE        (read-only) the context's device
  *   LOGAN_OPT_MIGRATION_MB  band-state migration budget (below)
  *   LOGAN_OPT_CONCURRENT    concurrent start levels (below)
- *   LOGAN_OPT_LONG_ITEM     one-extension-per-warp forms for long items (below)
+ *   LOGAN_OPT_LONG_ITEM     latency forms for long items (below)
  */
 #define LOGAN_OPT_GRAPHS 1
 #define LOGAN_OPT_TIMING 2
@@ -230,11 +230,12 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                                     0: level after level on the caller stream */
 #define LOGAN_OPT_LONG_ITEM 10   /* extensions starting at window levels 0-3
                                     run either several to a warp (most) or
-                                    one to a warp with the same window (fewer
+                                    in the level's latency form: one to a
+                                    warp with the same window (fewer
                                     instructions per anti-diagonal: what a
                                     long extension, which a batch waits for,
                                     or a batch too small to fill the GPU
-                                    needs).  v >= 0: one to a warp when
+                                    needs).  v >= 0: latency form when
                                     m + n >= v; -1: never; -2 (default):
                                     automatic -- every item when the batch
                                     has at most 32 items per SM, else
@@ -253,7 +254,7 @@ int logan_level_info(int level, int *window_cells, int *threads_per_unit);
  * synchronises on those events).
  *   level_ms[k]  device time of window level k (k < logan_num_levels()):
  *                its phase-1 launch plus its phase-2 launch (and those of
- *                its one-warp form), each counted only if it had entries to
+ *                its latency form), each counted only if it had entries to
  *                process; with
  *                LOGAN_OPT_CONCURRENT the phase-1 launches overlap, so the
  *                levels' times can add up to more than total_ms;

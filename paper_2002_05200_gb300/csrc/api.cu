@@ -20,7 +20,7 @@ namespace {
 
 constexpr size_t kAlign = 256;
 constexpr int kEvSets = 32;        // timed calls whose events are kept
-// Launch units: the window levels (0 .. kNumLevels-1), then the one-warp
+// Launch units: the window levels (0 .. kNumLevels-1), then the latency
 // forms of levels 0 .. kTwinLevels-1 (unit kNumLevels + k).
 constexpr int kUnits = kNumLevels + kTwinLevels;
 inline int unit_queue(int u) { return u < kNumLevels ? u : twin_queue(u - kNumLevels); }
@@ -64,7 +64,7 @@ struct logan_ctx {
     int blocks_per_sm[kNumLevels] = {};
     int twin_blocks_per_sm[kTwinLevels] = {};
     // LOGAN_OPT_LONG_ITEM: m + n from which items of levels < kTwinLevels
-    // take the one-warp form; -1 never, -2 automatic
+    // take the latency form; -1 never, -2 automatic
     int64_t long_item = -2;
     int8_t next_level[kNumLevels] = {};
     // timing: the events of the last kEvSets timed calls (ring)
@@ -193,12 +193,12 @@ int launch_unit(logan_ctx* c, int u, const KernelArgs& ka, int phase, cudaStream
     return e == cudaSuccess ? LOGAN_OK : LOGAN_ECUDA;
 }
 
-// threshold of m + n for the one-warp forms in a batch of n_items items
+// threshold of m + n for the latency forms in a batch of n_items items
 uint32_t long_item_min(const logan_ctx* c, uint32_t n_items) {
     if (c->long_item == -1) return 0xffffffffu;
     if (c->long_item >= 0) return uint32_t(std::min<int64_t>(c->long_item, 0xfffffffe));
     // automatic: a batch that cannot fill the GPU's warps runs every item in
-    // one-warp form; otherwise items of 64K bases and more do
+    // latency form; otherwise items of 64K bases and more do
     return n_items <= uint32_t(c->num_sms) * 32u ? 0u : 65536u;
 }
 
@@ -326,7 +326,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         ++launches;
     } else {
         // phase 1: every queue's binned items; the queues share no entry, so
-        // they run concurrently on their own streams, the one-warp forms
+        // they run concurrently on their own streams, the latency forms
         // (long items) first
         AuxSet* ax = c->concurrent ? aux_for(c, s) : nullptr;
         if (ax && cudaEventRecord(ax->fork, s) != cudaSuccess) return LOGAN_ECUDA;
@@ -346,7 +346,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         }
     }
     // phase 2: escalated items, narrowest level first (a queue only receives
-    // items from narrower levels); a level's one-warp form after the level
+    // items from narrower levels); a level's latency form after the level
     for (int lvl = (plain ? first + 1 : 0); lvl <= maxl; ++lvl) {
         for (int u : {lvl, lvl < kTwinLevels && !plain ? kNumLevels + lvl : -1}) {
             if (u < 0) continue;
@@ -671,7 +671,7 @@ int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
     std::memset(st, 0, sizeof(*st));
     const Counters& h = c->hcounters[call % kEvSets];
     // a launch counts only if it had entries to process: an empty launch's
-    // span is mostly its wait for room on the SMs; a one-warp form's time
+    // span is mostly its wait for room on the SMs; a latency form's time
     // and items count for its level
     for (int u = 0; u < kUnits; ++u) {
         const int q = unit_queue(u), l = unit_level(u);

@@ -79,13 +79,15 @@ __host__ __device__ constexpr int level_threads(int k) {
 }
 __host__ __device__ constexpr int level_window(int k) { return level_cells(k) * level_threads(k); }
 
-// One-warp forms.  Levels 0..kTwinLevels-1 put several extensions in a warp,
+// Latency forms.  Levels 0..kTwinLevels-1 put several extensions in a warp,
 // which keeps the lanes busy but makes every anti-diagonal step of one
 // extension cost a whole warp's instructions.  A long item (the one a
 // batch waits for) or an item of a batch too small to fill the GPU runs
-// instead in the level's one-warp form: the same window, G = 32 lanes of
-// window/32 rows each, so a step is about half the instructions and its
-// reductions are single warp reductions.
+// instead in its level's latency form: the same window, one warp of 32
+// lanes x window/32 rows, so a step is about half the instructions and its
+// reductions are single warp reductions.  (A 4-warp block form of the
+// 512-row level, one barrier per step, measured 2x slower per step than
+// its one-warp kernel, so levels 4 and up have none.)
 constexpr int kTwinLevels = 4;
 __host__ __device__ constexpr int twin_cells(int k) { return level_window(k) / 32; }
 

@@ -142,7 +142,7 @@ __device__ __forceinline__ int item_level(const Item& it, LevelTable table, int 
     return min(l, maxl);
 }
 
-// queue of an item: its starting level, or that level's one-warp form for a
+// queue of an item: its starting level, or that level's latency form for a
 // long item; -1 when the X-class filter leaves it out
 __device__ __forceinline__ int item_queue(const Item& it, LevelTable table, int force, int maxl) {
     const int l = item_level(it, table, force, maxl);

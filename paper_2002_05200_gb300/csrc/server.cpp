@@ -425,7 +425,7 @@ int logan_server_create(logan_ctx_t* ctx, size_t budget_bytes, int max_inflight,
     // a request is small next to the GPU but shares it with the other
     // slots: the scheduler picks LOGAN_OPT_LONG_ITEM per request from the
     // load (the automatic rule would put every item of a small request in
-    // the one-extension-per-warp forms)
+    // the latency forms)
     logan_set_option(ctx, LOGAN_OPT_LONG_ITEM, 65536);
     s->th = std::thread(scheduler, s);
     *out = s;

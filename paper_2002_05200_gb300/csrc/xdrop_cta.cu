@@ -1,7 +1,7 @@
 // X-drop extension with a multi-warp unit per extension (window level 6:
 // 128 threads x 16 rows, level 7: 512 threads x 8 rows, in registers).
 //
-// Same cell update as the one-warp kernel (paper Sec. III-A recurrence and
+// Same cell update as the G-lane kernels (paper Sec. III-A recurrence and
 // X-drop rule, Algorithm 2), with the anti-diagonal split across warps as in
 // the paper's segmented scheme (Sec. IV-A), except that every segment is
 // resident at once: thread t of the unit owns cells i = base + t*C + k.
@@ -303,17 +303,19 @@ __device__ bool cta_extend(const KernelArgs& ka, uint32_t id, int level, const E
 }
 
 template <int C, int NW>
-__global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int level, int phase) {
+__global__ void __launch_bounds__(NW * 32)
+    k_cta_persistent(KernelArgs ka, int level, int queue, int phase) {
     __shared__ CtaSmem<C, NW> sm;
     const bool plain = phase == PHASE_PLAIN;
-    const uint32_t* q = ka.queues + size_t(level) * ka.qcap;
+    const bool twin = queue != level;  // (no latency forms at these levels)
+    const uint32_t* q = ka.queues + size_t(queue) * ka.qcap;
     for (;;) {
         if (threadIdx.x == 0) {
             if (plain) {
                 const unsigned int s = atomicAdd(&ka.counters->head[level], 1u);
                 sm.slot = s < ka.n_items ? s : ~0u;
             } else {
-                sm.slot = pop_slot(ka.counters, level, phase);
+                sm.slot = pop_slot(ka.counters, queue, phase);
             }
         }
         __syncthreads();
@@ -342,9 +344,9 @@ __global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int l
         if (threadIdx.x == 0) {
             if (cells_here) atomicAdd(&ka.counters->cells[level], cells_here);
             if (ovf) {
-                const int nl = escalate(ka, level);
-                const unsigned int tl = atomicAdd(&ka.counters->tail[nl], 1u);
-                ka.queues[size_t(nl) * ka.qcap + tl] = id;
+                const int nq = escalate_queue(ka, level, twin);
+                const unsigned int tl = atomicAdd(&ka.counters->tail[nq], 1u);
+                ka.queues[size_t(nq) * ka.qcap + tl] = id;
             } else {
                 ka.ext[id] = r;
             }
@@ -358,8 +360,8 @@ __global__ void __launch_bounds__(NW * 32) k_cta_persistent(KernelArgs ka, int l
 cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int phase,
                              cudaStream_t s) {
     switch (level) {
-        case 6: k_cta_persistent<16, 4><<<grid, 128, 0, s>>>(ka, level, phase); break;
-        case 7: k_cta_persistent<8, 16><<<grid, 512, 0, s>>>(ka, level, phase); break;
+        case 6: k_cta_persistent<16, 4><<<grid, 128, 0, s>>>(ka, level, level, phase); break;
+        case 7: k_cta_persistent<8, 16><<<grid, 512, 0, s>>>(ka, level, level, phase); break;
         default: return cudaErrorInvalidValue;
     }
     return cudaGetLastError();

@@ -459,7 +459,7 @@ __global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) 
     const int lane = threadIdx.x & 31;
     const int gl = lane % G, unit = lane / G;
     const bool plain = phase == PHASE_PLAIN;
-    const bool twin = queue != level;  // level's one-warp form
+    const bool twin = queue != level;  // the level's latency form
     const uint32_t* q = ka.queues + size_t(queue) * ka.qcap;
     // plain form: one fixed item per unit, in input order
     const uint32_t plain_id =
