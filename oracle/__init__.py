@@ -1,13 +1,16 @@
 """CPU oracle for batched X-drop seed extension -- TEST INFRASTRUCTURE ONLY.
 
-Loads ``xdrop_oracle.c`` (compiled with the host C compiler into
-``oracle/_build/liboracle.so``) through ctypes.  Only the tests, the smoke
+Loads ``xdrop_oracle.c`` (linear gaps, the paper's method) and
+``xdrop_affine_oracle.c`` (the same extension with affine gaps) compiled
+with the host C compiler into ``oracle/_build/liboracle.so`` through ctypes.  Only the tests, the smoke
 check and the CPU-baseline leg of ``bench.py`` may use it; the library and
 its Python binding never import it.  It shares no code with the CUDA path.
 
 Every function follows the passages and readings listed at the top of
-``xdrop_oracle.c``.  Parity status: pinned (brute-force full DP at X = inf,
-closed forms, invariants and hand-derived worked examples in tests/).
+``xdrop_oracle.c`` (``affine_*``: of ``xdrop_affine_oracle.c``).  Parity
+status: pinned (brute-force full DP at X = inf, closed forms, invariants
+and hand-derived worked examples in tests/; the affine extension also
+against the linear one at gap_open = 0).
 """
 from __future__ import annotations
 
@@ -20,6 +23,7 @@ import numpy as np
 
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "xdrop_oracle.c")
+_SRC_AFFINE = os.path.join(_HERE, "xdrop_affine_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
@@ -39,10 +43,11 @@ def build(force: bool = False) -> str:
     """Compile the oracle with the host C compiler (gcc -O2, no -march flags)."""
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or \
-            os.path.getmtime(_LIB_PATH) < os.path.getmtime(_SRC):
+            os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
+                                              os.path.getmtime(_SRC_AFFINE)):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC])
+                               "-o", tmp, _SRC, _SRC_AFFINE])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -65,6 +70,17 @@ def lib():
         L.oracle_batch.restype = ctypes.c_int
         L.oracle_params_valid.argtypes = [i64, i64, i64, i64]
         L.oracle_params_valid.restype = ctypes.c_int
+        L.oracle_affine_extend.argtypes = [p, i64, p, i64, i64, i64, i64, i64, i64,
+                                           ctypes.POINTER(_Ext)]
+        L.oracle_affine_extend.restype = ctypes.c_int
+        L.oracle_affine_pair.argtypes = [p, i64, p, i64, i64, i64, i64, i64, i64, i64, i64,
+                                         i64, p]
+        L.oracle_affine_pair.restype = ctypes.c_int
+        L.oracle_affine_batch.argtypes = [p, p, p, ctypes.c_uint32, p, p, p, ctypes.c_uint32,
+                                          p, i64, i64, i64, i64, i64, i64, p, ctypes.c_int, p]
+        L.oracle_affine_batch.restype = ctypes.c_int
+        L.oracle_affine_params_valid.argtypes = [i64, i64, i64, i64, i64]
+        L.oracle_affine_params_valid.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -140,3 +156,59 @@ def run_batch(b, threads: Optional[int] = None):
         raise ValueError("the oracle reads ASCII pools: use b.subset(...) of a packed batch")
     return batch(b.poolA, b.offA, b.lenA, b.poolB, b.offB, b.lenB, b.seeds, b.match,
                  b.mismatch, b.gap, b.X, b.Xs, threads)
+
+
+# ---- affine gaps (xdrop_affine_oracle.c) ----
+
+def affine_extend(a: bytes, b: bytes, match: int = 1, mismatch: int = -1, gap_open: int = -2,
+                  gap_extend: int = -1, X: int = 50):
+    """One affine-gap X-drop extension (a gap of length L scores
+    gap_open + L * gap_extend).  Returns (best, bi, bj, cells)."""
+    out = _Ext()
+    rc = lib().oracle_affine_extend(_buf(a), len(a), _buf(b), len(b), match, mismatch,
+                                    gap_open, gap_extend, X, ctypes.byref(out))
+    if rc:
+        raise MemoryError("oracle extension could not allocate")
+    return out.best, out.bi, out.bj, out.cells
+
+
+def affine_pair(A: bytes, B: bytes, posA: int, posB: int, k: int, match: int = 1,
+                mismatch: int = -1, gap_open: int = -2, gap_extend: int = -1,
+                X: int = 50) -> np.void:
+    r = np.zeros(1, dtype=PAIR_DTYPE)
+    lib().oracle_affine_pair(_buf(A), len(A), _buf(B), len(B), posA, posB, k, match, mismatch,
+                             gap_open, gap_extend, X, r.ctypes.data)
+    return r[0]
+
+
+def affine_params_valid(match: int, mismatch: int, gap_open: int, gap_extend: int,
+                        X: int) -> bool:
+    return bool(lib().oracle_affine_params_valid(match, mismatch, gap_open, gap_extend, X))
+
+
+def run_batch_affine(b, gap_open: int, gap_extend: int, threads: Optional[int] = None):
+    """Every pair of a synth.Batch-like object (ASCII pools) with affine gaps
+    (b.gap is ignored).  Returns (PAIR_DTYPE results, threads used)."""
+    if getattr(b, "packed", False):
+        raise ValueError("the oracle reads ASCII pools: use b.subset(...) of a packed batch")
+    poolA = np.ascontiguousarray(b.poolA, dtype=np.uint8)
+    poolB = np.ascontiguousarray(b.poolB, dtype=np.uint8)
+    offA = np.ascontiguousarray(b.offA, dtype=np.uint64)
+    offB = np.ascontiguousarray(b.offB, dtype=np.uint64)
+    lenA = np.ascontiguousarray(b.lenA, dtype=np.uint32)
+    lenB = np.ascontiguousarray(b.lenB, dtype=np.uint32)
+    sd = np.ascontiguousarray(
+        np.stack([b.seeds[f] for f in ("idxA", "idxB", "posA", "posB", "len")], axis=1)
+        .astype(np.uint32))
+    n = sd.shape[0]
+    out = np.zeros(n, dtype=PAIR_DTYPE)
+    xs = None if b.Xs is None else np.ascontiguousarray(b.Xs, dtype=np.int32)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    used = lib().oracle_affine_batch(poolA.ctypes.data, offA.ctypes.data, lenA.ctypes.data,
+                                     lenA.size, poolB.ctypes.data, offB.ctypes.data,
+                                     lenB.ctypes.data, lenB.size, sd.ctypes.data, n,
+                                     b.match, b.mismatch, gap_open, gap_extend, b.X,
+                                     None if xs is None else xs.ctypes.data, int(threads),
+                                     out.ctypes.data)
+    return out, used
