@@ -47,6 +47,7 @@ METRIC = "X-drop GCUPS (computed cells), batched vs plain launch; serving p50/p9
 PROFILED_TRAFFIC = {"level": 2, "bytes": 114.5024e6 + 7.313408e6, "items": 48_000,
                     "sources": ("xdrop_group.cu", "logan_dev.cuh", "internal.h"),
                     "sha1": "39a79ed90010a0f473a11e6e5985226dd01e8535"}
+OPS_PER_CELL_AFFINE = 12  # Gotoh per cell: compare, diag add, E: 2 adds + max, F: 2 adds + max, 2 max, X-drop compare, select
 OPS_PER_CELL = 8          # Algorithm 2 per cell: compare, add, 2 gap adds, 2 max, X-drop compare, select
 LANES_PER_SM = 128        # nominal: 4 sub-partitions x 32 lanes per clock (Blackwell SM)
 
@@ -74,6 +75,10 @@ def parse():
     ap.add_argument("--kernel-only", action="store_true",
                     help="only the timed persistent steps (for profiler runs)")
     ap.add_argument("--no-serving", action="store_true")
+    ap.add_argument("--gap-open", type=int, default=None,
+                    help="affine gaps: time logan_extend_batch_affine with this gap_open "
+                         "(and --gap-extend) instead of the linear path")
+    ap.add_argument("--gap-extend", type=int, default=-1)
     ap.add_argument("--concurrent", type=int, default=1, choices=[0, 1],
                     help="1: the start levels of a batch run concurrently (default); "
                          "0: level after level on one stream")
@@ -330,6 +335,107 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+def affine_main(args, b, A, B, S, Xs, ctx, ws, out, stream, timed, rank, world, local, packed):
+    """The affine-gap path on the same workload: persistent time, e2e and the
+    affine oracle on the host cores; one JSON line."""
+    import torch
+
+    from paper_2002_05200_gb300 import logan, shard
+    go, ge = args.gap_open, args.gap_extend
+
+    def step():
+        ctx.extend_affine(A, B, S, b.match, b.mismatch, go, ge, b.X, Xs, workspace=ws, out=out,
+                          stream=stream)
+
+    with ClockSampler(local) as clk:
+        ms = timed(step, args.steps, args.warmup)
+    res = logan.results_to_numpy(out)
+    ok = res["status"] == 0
+    cells = int(res["cells"][ok].sum())
+    tot_cells = cells
+    if world > 1:
+        _, tot_cells = shard.reduce_step(0.0, cells, device=f"cuda:{local}")
+    value = tot_cells / (ms * 1e-3) / 1e9
+    clocks = clk.summary()
+    peak = logan.intpeak(local, 1, 2000)[0] / 1e9
+    achieved = OPS_PER_CELL_AFFINE * cells / (ms * 1e-3) / 1e9
+    n_pools = 1 if B is A else 2
+    launches = n_pools + (0 if packed else n_pools) + 1 + 3 + 3 + 1 + 1
+    cfg = workload_config(b, args.workload, args.pairs)
+    cfg["scoring"] = {"match": b.match, "mismatch": b.mismatch, "gap_open": go, "gap_extend": ge}
+    cfg["path"] = "affine gaps (logan_extend_batch_affine)"
+    line = {"metric": METRIC + " -- affine-gap path", "value": value, "unit": "GCUPS",
+            "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic", "config": cfg, "clocks": clocks,
+            "gpu_launches": launches * args.steps, "cells_per_step": tot_cells,
+            "erange_pairs": int((res["status"] == logan.ERANGE).sum())}
+    line["roofline"] = {
+        "bound": "alu", "kernel": "affine levels (whole step: 3 window levels + pre/post)",
+        "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+        "traffic": None, "ops_per_cell": OPS_PER_CELL_AFFINE, "cells": cells,
+        "launch_ms": ms,
+        "peak_basis": "measured: int32 max chains on all SMs (logan_intpeak op 1); of measured"}
+    if not args.no_e2e:
+        hA = {k: v.cpu().pin_memory() for k, v in (("bases", A.bases), ("off", A.offsets),
+                                                   ("len", A.lengths))}
+        shared = B is A
+        hB = hA if shared else {k: v.cpu().pin_memory() for k, v in (
+            ("bases", B.bases), ("off", B.offsets), ("len", B.lengths))}
+        hS = S.cpu().pin_memory()
+        hX = Xs.cpu().pin_memory() if Xs is not None else None
+        hout = torch.empty_like(out, device="cpu").pin_memory()
+        dA = logan.DevicePool(torch.empty_like(A.bases), torch.empty_like(A.offsets),
+                              torch.empty_like(A.lengths), packed, A.pool_bases)
+        dB = dA if shared else logan.DevicePool(
+            torch.empty_like(B.bases), torch.empty_like(B.offsets), torch.empty_like(B.lengths),
+            packed, B.pool_bases)
+        dS = torch.empty_like(S)
+        dX = torch.empty_like(Xs) if Xs is not None else None
+        h2d = sum(t.numel() * t.element_size()
+                  for t in list(hA.values()) + ([] if shared else list(hB.values())) + [hS] +
+                  ([hX] if hX is not None else []))
+
+        def e2e_step():
+            with torch.cuda.stream(stream):
+                for h, d in ((hA, dA),) if shared else ((hA, dA), (hB, dB)):
+                    d.bases.copy_(h["bases"], non_blocking=True)
+                    d.offsets.copy_(h["off"], non_blocking=True)
+                    d.lengths.copy_(h["len"], non_blocking=True)
+                dS.copy_(hS, non_blocking=True)
+                if dX is not None:
+                    dX.copy_(hX, non_blocking=True)
+                ctx.extend_affine(dA, dB, dS, b.match, b.mismatch, go, ge, b.X, dX,
+                                  workspace=ws, out=out, stream=stream)
+                hout.copy_(out, non_blocking=True)
+
+        ms_e2e = timed(e2e_step, args.steps, 1)
+        same = bool(np.array_equal(hout.numpy().view(logan.RESULT_DTYPE).reshape(-1), res))
+        line["e2e"] = {"value": tot_cells / (ms_e2e * 1e-3) / 1e9, "unit": "GCUPS",
+                       "h2d_bytes_per_step": int(h2d),
+                       "d2h_bytes_per_step": int(hout.numel() * hout.element_size()),
+                       "ms_per_step": ms_e2e, "results_identical": same}
+    if rank == 0 and not args.no_cpu_baseline:
+        import oracle
+        threads = os.cpu_count() or 1
+        chunk = max(threads * 4, 64)
+        done, ccells, t0 = 0, 0, time.perf_counter()
+        while done < b.n_pairs:
+            sub = b.subset(np.arange(done, min(done + chunk, b.n_pairs)))
+            r, used = oracle.run_batch_affine(sub, go, ge, threads)
+            ccells += int(r["cells"][r["status"] == 0].sum())
+            done += sub.n_pairs
+            if time.perf_counter() - t0 >= args.cpu_seconds:
+                break
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": ccells / dt / 1e9, "unit": "GCUPS", "cores": used,
+                                "kind": "oracle",
+                                "sample": f"first {done} of {b.n_pairs} pairs ({ccells} cells, "
+                                          f"{dt:.1f} s), affine oracle, all host cores"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def main():
     args = parse()
     if args.pairs is None:
@@ -410,6 +516,10 @@ def main():
         if world > 1:
             ms, _ = shard.reduce_step(ms, 0, device=f"cuda:{local}")
         return ms / steps
+
+    if args.gap_open is not None:
+        return affine_main(args, b, A, B, S, Xs, ctx, ws, out, stream, timed, rank, world, local,
+                           packed)
 
     # persistent form, with per-level events kept for every timed step
     ctx.set_option(logan.OPT_TIMING, 1)

@@ -163,6 +163,35 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                              logan_result_t *out, void *stream);
 
 /*
+ * The same seeded extension with affine gaps (the paper uses a linear gap,
+ * Sec. III-A, and names other scoring schemes as future work, Sec. VIII):
+ * a gap of length L scores gap_open + L * gap_extend, i.e. Gotoh's three
+ * states per cell
+ *   E(i,j) = max(E(i,j-1) + gap_extend, H(i,j-1) + gap_open + gap_extend)
+ *   F(i,j) = max(F(i-1,j) + gap_extend, H(i-1,j) + gap_open + gap_extend)
+ *   H(i,j) = max(H(i-1,j-1) + match/mismatch, E(i,j), F(i,j)),
+ * with the X-drop rule on H (a pruned cell loses all three states) and the
+ * same sweep, band trimming, best cell, split at the seed, seed score and
+ * result fields as logan_extend_batch.
+ *   match/mismatch: as logan_extend_batch; gap_open, gap_extend: added
+ *   scores, -1000 <= v <= 0; X, X_per_pair, workspace (logan_workspace_size
+ *   bytes), out, stream: as logan_extend_batch.
+ * Per pair, max(|match|, |mismatch|, |gap_open| + |gap_extend|) * (m + n)
+ * + X must stay below 2^29 (else LOGAN_EINVAL for the pair).  Bands are
+ * held in windows of 64, 256 and 512 rows; a pair whose band outgrows 512
+ * rows, or whose X exceeds 2^20 - 4096, gets status LOGAN_ERANGE.  Runs on
+ * `stream` (no graphs, no timing statistics).  Returns LOGAN_EINVAL for
+ * invalid scalars or pointers, LOGAN_ENOMEM if ws_bytes is too small,
+ * LOGAN_ECUDA on a launch failure.
+ */
+int logan_extend_batch_affine(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
+                              const logan_seqs_t *seqsB, const logan_seed_t *seeds,
+                              uint32_t n_pairs, int32_t match, int32_t mismatch,
+                              int32_t gap_open, int32_t gap_extend, int32_t X,
+                              const int32_t *X_per_pair, void *workspace, size_t ws_bytes,
+                              logan_result_t *out, void *stream);
+
+/*
  * Same operation and results as logan_extend_batch, for callers that cannot
  * allocate device memory -- e.g. a host whose GPU memory is owned by another
  * allocator, or a latency-critical loop that must not call cudaMalloc /

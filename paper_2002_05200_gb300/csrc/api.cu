@@ -63,6 +63,7 @@ struct logan_ctx {
     LevelTable table{};
     int blocks_per_sm[kNumLevels] = {};
     int twin_blocks_per_sm[kTwinLevels] = {};
+    int affine_blocks_per_sm[4] = {};
     // LOGAN_OPT_LONG_ITEM: m + n from which items of levels < kTwinLevels
     // take the latency form; -1 never, -2 automatic
     int64_t long_item = -2;
@@ -227,10 +228,16 @@ AuxSet* aux_for(logan_ctx* c, cudaStream_t s) {
 
 // The whole pipeline on `s` (no synchronisation).  plain != 0: one-launch
 // form at c->plain_level, in input order.
+// aff != nullptr: affine gaps (gap_open, gap_extend), through the affine
+// window levels instead of the linear ones.
+struct AffineGaps {
+    int32_t open, extend;
+};
+
 int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
                  const logan_seed_t* seeds, uint32_t n_pairs, Scoring sc, int32_t X,
                  const int32_t* Xs, char* ws, const Layout& L, logan_result_t* out,
-                 cudaStream_t s, int plain, bool timing) {
+                 cudaStream_t s, int plain, bool timing, const AffineGaps* aff = nullptr) {
     PoolDev pa = {A->bases, A->offsets, A->lengths, A->count, A->packed2bit, A->pool_bases,
                   A->packed2bit ? static_cast<const uint32_t*>(A->bases)
                                 : reinterpret_cast<const uint32_t*>(ws + L.wordsA),
@@ -269,10 +276,16 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         e = launch_split(pa, pb, seeds, n_pairs, sc, X, Xs, items, info, ext,
                          reinterpret_cast<int32_t*>(ws + L.mig_slot), s);
     ++launches;
-    const int maxl = int(c->max_level);
+    const int maxl = aff ? kNumLevels - 1 : int(c->max_level);
     LevelTable tab = c->table;
     tab.max_level = maxl;
     tab.long_min = long_item_min(c, 2u * n_pairs);
+    if (aff) {
+        // one queue, longest first; X too large for the affine keys goes to
+        // queue kWarpLevels and is rejected
+        tab.only_xclass = -1;
+        tab.long_min = 0xffffffffu;
+    }
     int first = 0;
     if (e == cudaSuccess) {
         if (plain) {
@@ -280,7 +293,9 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
             e = launch_reset_counters(counters, n_items, first, s);
             ++launches;
         } else {
-            const int force = c->force_level >= 0 ? int(std::min<int64_t>(c->force_level, maxl)) : -1;
+            const int force = aff ? 0
+                              : c->force_level >= 0 ? int(std::min<int64_t>(c->force_level, maxl))
+                                                    : -1;
             e = launch_bin(items, n_items, tab, force, reinterpret_cast<uint32_t*>(ws + L.hist), queues,
                            n_items, counters, s);
             launches += 3;
@@ -309,6 +324,21 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         ka.mig_pool[l] = L.mig_cap[l] ? reinterpret_cast<int32_t*>(ws + L.mig_pool[l]) : nullptr;
     }
     ka.mig_slot = reinterpret_cast<int32_t*>(ws + L.mig_slot);
+    if (aff) {
+        // affine levels, narrowest first (each receives the bands that
+        // outgrew the previous one), then the rejected items, then combine
+        for (int l = 0; l < affine_levels(); ++l) {
+            const int grid = c->num_sms * std::max(1, c->affine_blocks_per_sm[l]);
+            if (launch_affine_level(l, ka, aff->open, aff->extend, grid, s) != cudaSuccess)
+                return LOGAN_ECUDA;
+            ++launches;
+        }
+        if (launch_affine_reject(ka, kWarpLevels, s) != cudaSuccess ||
+            launch_combine(seeds, info, ext, n_pairs, out, s) != cudaSuccess)
+            return LOGAN_ECUDA;
+        c->launches_last = launches + 2;
+        return LOGAN_OK;
+    }
     uint32_t p1_levels = 0, p2_levels = 0;
     cudaEvent_t* ev = c->ev;
     auto rec = [&](int idx, cudaStream_t st) {
@@ -532,6 +562,7 @@ int logan_ctx_create(logan_ctx_t** out, int device, const char* autotune_json) {
     for (int l = 0; l < kNumLevels; ++l)
         c->blocks_per_sm[l] = l < kWarpLevels ? warp_level_blocks_per_sm(l) : cta_level_blocks_per_sm(l);
     for (int l = 0; l < kTwinLevels; ++l) c->twin_blocks_per_sm[l] = twin_blocks_per_sm(l);
+    for (int l = 0; l < affine_levels(); ++l) c->affine_blocks_per_sm[l] = affine_blocks_per_sm(l);
     for (auto& set : c->evs)
         for (auto& ev : set)
             if (cudaEventCreate(&ev) != cudaSuccess) {
@@ -597,6 +628,30 @@ int logan_extend_batch_plain(logan_ctx_t* c, const logan_seqs_t* A, const logan_
                              size_t ws_bytes, logan_result_t* out, void* stream) {
     return extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs, ws, ws_bytes, out,
                          stream, 1);
+}
+
+int logan_extend_batch_affine(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
+                              const logan_seed_t* seeds, uint32_t n_pairs, int32_t match,
+                              int32_t mismatch, int32_t gap_open, int32_t gap_extend, int32_t X,
+                              const int32_t* Xs, void* ws, size_t ws_bytes, logan_result_t* out,
+                              void* stream) {
+    if (!c || !pool_ok(A) || !pool_ok(B)) return LOGAN_EINVAL;
+    // gap_open + gap_extend is the largest single-step gap penalty: the
+    // per-pair range check of the split uses it like the linear gap
+    if (!params_ok(match, mismatch, gap_extend, X) || gap_open > 0 ||
+        gap_open < -kMaxParam)
+        return LOGAN_EINVAL;
+    if (n_pairs > 0x7fffffffu) return LOGAN_EINVAL;
+    if (n_pairs == 0) return LOGAN_OK;
+    if (!seeds || !out || !ws) return LOGAN_EINVAL;
+    if (reinterpret_cast<uintptr_t>(ws) % kAlign) return LOGAN_EINVAL;
+    const Layout L = make_layout(c, A, B, n_pairs);
+    if (ws_bytes < L.total) return LOGAN_ENOMEM;
+    DeviceGuard g(c->device);
+    const Scoring sc = {match, mismatch, gap_open + gap_extend};
+    const AffineGaps aff = {gap_open, gap_extend};
+    return run_pipeline(c, A, B, seeds, n_pairs, sc, X, Xs, static_cast<char*>(ws), L, out,
+                        static_cast<cudaStream_t>(stream), 0, false, &aff);
 }
 
 int logan_set_option(logan_ctx_t* c, int option, int64_t v) {

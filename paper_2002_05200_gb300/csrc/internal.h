@@ -73,6 +73,12 @@ int twin_blocks_per_sm(int level);
 cudaError_t launch_cta_level(int level, const KernelArgs& ka, int grid, int phase, cudaStream_t s);
 int cta_level_blocks_per_sm(int level);
 cudaError_t launch_ring(const KernelArgs& ka, int grid, cudaStream_t s);
+// affine-gap window levels (xdrop_affine.cu): level l pops queue l
+int affine_levels();
+int affine_blocks_per_sm(int level);
+cudaError_t launch_affine_level(int level, const KernelArgs& ka, int gap_open, int gap_extend,
+                                int grid, cudaStream_t s);
+cudaError_t launch_affine_reject(const KernelArgs& ka, int queue, cudaStream_t s);
 
 // pre/post-processing kernels (prep.cu)
 struct PoolDev {

@@ -164,4 +164,33 @@ __device__ __forceinline__ uint32_t stream_code(const uint32_t* __restrict__ w, 
     return code_at(w, pos + (dir > 0 ? q : -q));
 }
 
+// 16 consecutive codes of pool positions s..s+15 (s >= 0; the pool keeps one
+// spare word after its last base), code of s in the low bits.
+__device__ __forceinline__ uint32_t load16(const uint32_t* __restrict__ w, int64_t s) {
+    const int64_t wi = s >> 4;
+    return __funnelshift_r(__ldg(w + wi), __ldg(w + wi + 1), uint32_t(s & 15) * 2u);
+}
+
+// reverses the order of the sixteen 2-bit codes of a word
+__device__ __forceinline__ uint32_t rev16(uint32_t x) {
+    x = __brev(x);
+    return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
+}
+
+// stream codes q..q+15 of an operand read from pool position pos in
+// direction dir (code q in the low bits); 0 for indices outside [0, len)
+__device__ __forceinline__ uint32_t stream_codes16(const uint32_t* __restrict__ w, int64_t pos,
+                                                   int dir, int len, int q) {
+    if (q < 0 || q >= len) return 0u;
+    if (dir > 0) return load16(w, pos + q);
+    const int64_t p = pos - q;  // position of code q; codes q+t sit at p-t
+    int64_t s = p - 15;
+    uint32_t sh = 0u;
+    if (s < 0) {
+        sh = uint32_t(-s) * 2u;
+        s = 0;
+    }
+    return rev16(load16(w, s)) >> sh;
+}
+
 }  // namespace logan

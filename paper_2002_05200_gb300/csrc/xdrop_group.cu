@@ -92,37 +92,12 @@ __device__ __forceinline__ uint32_t b_code(const KernelArgs& ka, const UState<C>
     return stream_code(ka.wb, u.bpos, u.dir, uint32_t(u.n), q);
 }
 
-// 16 consecutive codes of pool positions s..s+15 (s >= 0; the pool keeps one
-// spare word after its last base).
-__device__ __forceinline__ uint32_t load16(const uint32_t* __restrict__ w, int64_t s) {
-    const int64_t wi = s >> 4;
-    return __funnelshift_r(__ldg(w + wi), __ldg(w + wi + 1), uint32_t(s & 15) * 2u);
-}
-
-// reverses the order of the sixteen 2-bit codes of a word
-__device__ __forceinline__ uint32_t rev16(uint32_t x) {
-    x = __brev(x);
-    return ((x >> 1) & 0x55555555u) | ((x & 0x55555555u) << 1);
-}
-
 // b' stream codes q..q+15 in stream order (0 for indices outside [0, n)).
 template <int C>
 __device__ __forceinline__ uint32_t b_codes16(const KernelArgs& ka, const UState<C>& u, int q) {
-    if (q < 0 || q >= u.n) return 0u;
-    if (u.dir > 0) return load16(ka.wb, u.bpos + q);
-    const int64_t p = u.bpos - q;  // position of code q; codes q+t sit at p-t
-    int64_t s = p - 15;
-    uint32_t sh = 0u;
-    if (s < 0) {
-        sh = uint32_t(-s) * 2u;
-        s = 0;
-    }
-    return rev16(load16(ka.wb, s)) >> sh;
+    return stream_codes16(ka.wb, u.bpos, u.dir, u.n, q);
 }
 
-// max over the G lanes of a unit: one warp reduction for a whole-warp unit,
-// else a butterfly inside each G-lane segment (a reduction with a partial
-// lane mask per unit measured ~40 % slower at G = 8)
 template <int G>
 __device__ __forceinline__ int unit_max(int v) {
     if constexpr (G == 32) {

@@ -31,6 +31,7 @@ assert RESULT_DTYPE.itemsize == 40
 
 EXPORTED = ["logan_version", "logan_strerror", "logan_ctx_create", "logan_ctx_destroy",
             "logan_workspace_size", "logan_extend_batch", "logan_extend_batch_plain",
+            "logan_extend_batch_affine",
             "logan_set_option", "logan_get_option", "logan_num_levels", "logan_level_info",
             "logan_last_stats", "logan_call_stats", "logan_set_level_table",
             "logan_get_level_table", "logan_intpeak", "logan_autotune", "logan_autotune_save",
@@ -100,6 +101,7 @@ def lib():
                     p, ctypes.c_size_t, p, p]
         L.logan_extend_batch.argtypes = ext_args
         L.logan_extend_batch_plain.argtypes = ext_args
+        L.logan_extend_batch_affine.argtypes = ext_args[:7] + [ctypes.c_int32] + ext_args[7:]
         L.logan_set_option.argtypes = [p, ctypes.c_int, i64]
         L.logan_get_option.argtypes = [p, ctypes.c_int, ctypes.POINTER(i64)]
         L.logan_level_info.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -308,6 +310,28 @@ class Context:
                 workspace.data_ptr(), workspace.numel(), out.data_ptr(),
                 ctypes.c_void_p(stream.cuda_stream))
         _check(rc, "logan_extend_batch_plain" if plain else "logan_extend_batch")
+        return out[:n]
+
+    def extend_affine(self, A: DevicePool, B: DevicePool, seeds, match: int = 1,
+                      mismatch: int = -1, gap_open: int = -2, gap_extend: int = -1, X: int = 50,
+                      X_per_pair=None, workspace=None, out=None, stream=None):
+        """Runs logan_extend_batch_affine (a gap of length L scores
+        gap_open + L * gap_extend); returns the int32 [n, 10] result tensor."""
+        import torch
+        n = int(seeds.shape[0])
+        if out is None:
+            out = torch.empty((max(n, 1), 10), dtype=torch.int32, device=f"cuda:{self.device}")
+        if workspace is None:
+            workspace = self.workspace(A, B, n)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        ca, cb = A.c(), B.c()
+        rc = lib().logan_extend_batch_affine(
+            self._h, ctypes.byref(ca), ctypes.byref(cb), seeds.data_ptr() if n else None, n,
+            match, mismatch, gap_open, gap_extend, X,
+            X_per_pair.data_ptr() if X_per_pair is not None else None, workspace.data_ptr(),
+            workspace.numel(), out.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+        _check(rc, "logan_extend_batch_affine")
         return out[:n]
 
     def last_stats(self, back: int = 0) -> dict:

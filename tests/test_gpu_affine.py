@@ -1,0 +1,125 @@
+"""Affine-gap path (logan_extend_batch_affine) vs the affine CPU oracle,
+bit-exact on every integer field."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_05200_gb300 import logan, synth
+from tests.gpu_common import assert_same
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = logan.Context(0)
+    yield c
+    c.close()
+
+
+def run_affine(ctx, b, go, ge, packed2bit=False):
+    import torch
+    A, B, S, Xs = logan.batch_to_device(b, packed2bit=packed2bit)
+    out = ctx.extend_affine(A, B, S, b.match, b.mismatch, go, ge, b.X, Xs)
+    torch.cuda.synchronize()
+    return logan.results_to_numpy(out)
+
+
+def ref_affine(b, go, ge):
+    return oracle.run_batch_affine(b, go, ge)[0]
+
+
+@pytest.mark.parametrize("go,ge", [(-2, -1), (-5, -2), (0, -1), (-1, 0)])
+def test_uniform_pairs(ctx, go, ge):
+    b = synth.uniform_pairs(n_pairs=400)
+    assert_same(run_affine(ctx, b, go, ge), ref_affine(b, go, ge), f"uniform {go},{ge}")
+
+
+def test_lognormal_packed(ctx):
+    b = synth.lognormal_batch(n_pairs=300)
+    assert_same(run_affine(ctx, b, -2, -1, packed2bit=True), ref_affine(b, -2, -1), "lognormal")
+
+
+def test_uneven_per_pair_x(ctx):
+    b = synth.uneven_batch(n_pairs=200, max_len=30_000, seed=71)
+    assert_same(run_affine(ctx, b, -3, -1, packed2bit=True), ref_affine(b, -3, -1), "uneven")
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_tiny_edge_cases(ctx, seed):
+    b = synth.tiny_pairs(3000, 40, seed=seed)
+    assert_same(run_affine(ctx, b, -2, -1), ref_affine(b, -2, -1), "tiny")
+    assert_same(run_affine(ctx, b, -4, 0, packed2bit=True), ref_affine(b, -4, 0), "tiny packed")
+
+
+@pytest.mark.parametrize("scheme", [(2, -3, -4, -2), (1, -1, -1, -1), (5, -4, -10, -1),
+                                    (1000, -1000, -1000, -1000)])
+def test_scoring_schemes(ctx, scheme):
+    match, mismatch, go, ge = scheme
+    b = synth.uniform_pairs(n_pairs=200)
+    b.match, b.mismatch = match, mismatch
+    assert_same(run_affine(ctx, b, go, ge), ref_affine(b, go, ge), str(scheme))
+
+
+def test_zero_open_equals_linear_path(ctx):
+    import torch
+    b = synth.uneven_batch(n_pairs=150, max_len=8_000, seed=72)
+    A, B, S, Xs = logan.batch_to_device(b, packed2bit=True)
+    lin = ctx.extend(A, B, S, b.match, b.mismatch, -2, b.X, Xs)
+    aff = ctx.extend_affine(A, B, S, b.match, b.mismatch, 0, -2, b.X, Xs)
+    torch.cuda.synchronize()
+    assert np.array_equal(logan.results_to_numpy(lin), logan.results_to_numpy(aff))
+
+
+def test_wide_bands_report_erange(ctx):
+    # unpruned: a side's widest anti-diagonal has min(m, n) + 1 cells; above
+    # the 512-row window the pair is LOGAN_ERANGE, the rest are exact
+    b = synth.tiny_pairs(60, 1500, seed=8, X_choices=(200_000,))
+    g = run_affine(ctx, b, -2, -1)
+    ref = ref_affine(b, -2, -1)
+    s = b.seeds
+    lA, lB = b.lenA[s["idxA"]].astype(np.int64), b.lenB[s["idxB"]].astype(np.int64)
+    left = np.minimum(s["posA"], s["posB"]).astype(np.int64) + 1
+    right = np.minimum(lA - s["posA"] - s["len"], lB - s["posB"] - s["len"]) + 1
+    wide = np.maximum(left, right) > 512
+    assert wide.any() and (~wide).any()
+    assert np.all(g["status"][wide] == logan.ERANGE)
+    for f in ("score", "left", "right", "begA", "begB", "endA", "endB", "cells"):
+        assert np.array_equal(g[f][~wide].astype(np.int64), ref[f][~wide].astype(np.int64)), f
+
+
+def test_x_beyond_key_range_reports_erange(ctx):
+    b = synth.uniform_pairs(n_pairs=20)
+    b.Xs = np.full(b.n_pairs, (1 << 20), dtype=np.int32)
+    b.Xs[::2] = 50
+    g = run_affine(ctx, b, -2, -1)
+    assert np.all(g["status"][1::2] == logan.ERANGE)
+    ref = ref_affine(b.subset(np.arange(0, b.n_pairs, 2)), -2, -1)
+    assert_same(g[::2], ref, "small X")
+
+
+def test_argument_errors(ctx):
+    b = synth.uniform_pairs(n_pairs=4)
+    A, B, S, _ = logan.batch_to_device(b)
+    for args in ((1, -1, 1, -1, 5), (1, -1, -1, 1, 5), (1, -1, -1001, -1, 5), (1, 2, -1, -1, 5),
+                 (1, -1, -1, -1, -1)):
+        with pytest.raises(logan.LoganError) as e:
+            ctx.extend_affine(A, B, S, *args)
+        assert e.value.code == logan.EINVAL
+
+
+def test_lognormal_100k_sampled(ctx):
+    # the affine bench workload at full size, in its launch configuration
+    b = synth.lognormal_batch()
+    g = run_affine(ctx, b, -2, -1, packed2bit=True)
+    ok = g["status"] == logan.OK
+    assert np.all(ok | (g["status"] == logan.ERANGE))
+    rng = np.random.default_rng(201)
+    idx = np.unique(rng.choice(b.n_pairs, 300, replace=False))
+    assert_same(g[idx], ref_affine(b.subset(idx), -2, -1), "lognormal 100K sample")
+    k = b.seeds["len"].astype(np.int64)
+    assert np.array_equal(g["score"][ok].astype(np.int64),
+                          (g["left"].astype(np.int64) + k * b.match + g["right"])[ok])
