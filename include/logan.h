@@ -178,8 +178,9 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   bytes), out, stream: as logan_extend_batch.
  * Per pair, max(|match|, |mismatch|, |gap_open| + |gap_extend|) * (m + n)
  * + X must stay below 2^29 (else LOGAN_EINVAL for the pair).  Bands are
- * held in windows of 64, 256 and 512 rows; a pair whose band outgrows 512
- * rows, or whose X exceeds 2^20 - 4096, gets status LOGAN_ERANGE.  Runs on
+ * held in windows of 64, 128, 256 and 512 rows (the first by X: <= 35, <= 150,
+ * <= 300, larger); a pair whose band outgrows 512 rows, or whose X exceeds
+ * 2^20 - 4096, gets status LOGAN_ERANGE.  Runs on
  * `stream` (no graphs, no timing statistics).  Returns LOGAN_EINVAL for
  * invalid scalars or pointers, LOGAN_ENOMEM if ws_bytes is too small,
  * LOGAN_ECUDA on a launch failure.

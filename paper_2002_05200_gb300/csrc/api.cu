@@ -281,8 +281,11 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     tab.max_level = maxl;
     tab.long_min = long_item_min(c, 2u * n_pairs);
     if (aff) {
-        // one queue, longest first; X too large for the affine keys goes to
-        // queue kWarpLevels and is rejected
+        // affine windows 64 / 128 / 256 / 512 rows by X class, longest first;
+        // X too large for the affine keys goes to queue kWarpLevels and is
+        // rejected
+        const int8_t alv[kXClasses] = {0, 0, 1, 1, 2, 3, 3, 3};
+        for (int i = 0; i < kXClasses; ++i) tab.lv[i] = alv[i];
         tab.only_xclass = -1;
         tab.long_min = 0xffffffffu;
     }
@@ -293,9 +296,9 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
             e = launch_reset_counters(counters, n_items, first, s);
             ++launches;
         } else {
-            const int force = aff ? 0
-                              : c->force_level >= 0 ? int(std::min<int64_t>(c->force_level, maxl))
-                                                    : -1;
+            const int force = (!aff && c->force_level >= 0)
+                                  ? int(std::min<int64_t>(c->force_level, maxl))
+                                  : -1;
             e = launch_bin(items, n_items, tab, force, reinterpret_cast<uint32_t*>(ws + L.hist), queues,
                            n_items, counters, s);
             launches += 3;

@@ -13,9 +13,10 @@
 // registers; the loop is unrolled six times so that the three H arrays and
 // the two E / F arrays all rotate roles without moves.  Keys
 // (H - T_d) * W + (W - 1 - row) give the best and its tie-break in one max.
-// Levels: 64 rows (8 lanes x 8, four extensions per warp), 256 (32 x 8)
-// and 512 (32 x 16); a band outgrowing 512 rows gets LOGAN_ERANGE.  A band
-// that outgrows a window restarts at the next one.
+// Levels: 64 rows (8 lanes x 8, four extensions per warp), 128 (8 x 16,
+// four per warp), 256 (16 x 16, two per warp) and 512 (32 x 16); an item
+// starts at the level its X class maps to, a band that outgrows a window
+// restarts at the next one, and one outgrowing 512 rows gets LOGAN_ERANGE.
 #include "internal.h"
 
 #include "../../include/logan.h"
@@ -211,24 +212,41 @@ __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, ASt
     const int k0 = __viaddmin_s32_relu(rlo, -i0, C);     // clamp(rlo - i0, 0, C)
     const int k1 = __viaddmin_s32_relu(rhi, 1 - i0, C);  // clamp(rhi + 1 - i0, 0, C)
     const uint32_t rb = __funnelshift_lc(~0u, 0u, k1) & ~__funnelshift_lc(~0u, 0u, k0);
+    // the additions are multiply-adds with a run-time 1 and the substitution
+    // score is picked by a multiply (the row's match flag moved to the sign
+    // bit, then the high word of a product with 1), so that they run on the
+    // FMA pipe beside the ALU pipe's maxima and selects
+    const int one = ka.one;
+    const int dsub = ka.sc.mismatch - ka.sc.match;
+    // key = (h - T) * W + (C-1-k) = h * W + kbase - k, in wrapping unsigned
+    // arithmetic (h * W alone can exceed 32 bits; the key itself cannot)
+    const uint32_t kbase = uint32_t(C - 1) - uint32_t(T) * uint32_t(Gr::W);
+    const uint32_t wscale = uint32_t(one) * uint32_t(Gr::W);
     int lkey = -1;
     uint32_t bits = 0u;  // bit C-1-k: row k live
 #pragma unroll
-    for (int k = 0; k < C; ++k) {
-        const int uh = k ? H1[k - 1] : h1c;
-        const int uf = k ? F1[k - 1] : f1c;
-        const int dg = k ? H2[k - 1] : h2c;
-        const int e = __vimax3_s32(E1[k] + ge, H1[k] + goe, NEGA);
-        const int f = __vimax3_s32(uf + ge, uh + goe, NEGA);
-        const int t = dg + ((eq >> (2 * k)) & 1u ? ka.sc.match : ka.sc.mismatch);
-        const int h = __vimax3_s32(t, e, f);
-        const bool live = ((rb >> k) & 1u) && h >= T;
-        HO[k] = live ? h : NEGA;
-        EO[k] = live ? e : NEGA;
-        FO[k] = live ? f : NEGA;
-        // live: 0 <= h - T <= X + match, so the key stays below 2^31
-        lkey = max(lkey, live ? (h - T) * Gr::W + (C - 1 - k) : -1);
-        bits = (bits << 1) | (live ? 1u : 0u);
+    for (int k = 0; k < C; k += 2) {
+        int key[2];
+#pragma unroll
+        for (int hh = 0; hh < 2; ++hh) {
+            const int kk = k + hh;
+            const int uh = kk ? H1[kk - 1] : h1c;
+            const int uf = kk ? F1[kk - 1] : f1c;
+            const int dg = kk ? H2[kk - 1] : h2c;
+            const int e = __vimax3_s32(E1[kk] * one + ge, H1[kk] * one + goe, NEGA);
+            const int f = __vimax3_s32(uf * one + ge, uh * one + goe, NEGA);
+            const int y = __mulhi(int(eq * ka.pw[kk]), one);  // -1 on a match, else 0
+            const int t = y * dsub + (dg * one + ka.sc.mismatch);
+            const int h = __vimax3_s32(t, e, f);
+            const bool live = ((rb >> kk) & 1u) && h >= T;
+            HO[kk] = live ? h : NEGA;
+            EO[kk] = live ? e : NEGA;
+            FO[kk] = live ? f : NEGA;
+            // live: 0 <= h - T <= X + match, so the key stays below 2^31
+            key[hh] = live ? int(uint32_t(h) * wscale + (kbase - uint32_t(kk))) : -1;
+            bits = (bits << 1) | (live ? 1u : 0u);
+        }
+        lkey = __vimax3_s32(lkey, key[0], key[1]);
     }
     if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
     const int wkey = a_unit_max<G>(lkey >= 0 ? lkey + (G - 1 - gl) * C : -1);
@@ -262,11 +280,10 @@ __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, ASt
 }
 
 template <int G, int C>
-__global__ void __launch_bounds__(128) k_affine(KernelArgs ka, int go, int ge, int level,
+__global__ void __launch_bounds__(128, (C == 16) ? 3 : 4) k_affine(KernelArgs ka, int go, int ge, int level,
                                                 int n_levels) {
     const int lane = threadIdx.x & 31;
     const int gl = lane % G, unit = lane / G;
-    const int phase = level == 0 ? PHASE_INITIAL : PHASE_ESCALATED;
     const uint32_t* q = ka.queues + size_t(level) * ka.qcap;
     int P0[C], P1[C], P2[C], E0[C], E1[C], F0[C], F1[C];
 #pragma unroll
@@ -296,9 +313,13 @@ __global__ void __launch_bounds__(128) k_affine(KernelArgs ka, int go, int ge, i
             const uint32_t want = __ballot_sync(FULL, need && gl == 0);
             if (want) {
                 const int leader = __ffs(want) - 1;
+                // levels run one after another, so a level's queue (its
+                // binned items, then those escalated into it) is complete
                 unsigned int first = 0u, limit = 0u;
-                if (lane == leader)
-                    first = pop_slots(ka.counters, level, phase, unsigned(__popc(want)), &limit);
+                if (lane == leader) {
+                    first = atomicAdd(&ka.counters->head[level], unsigned(__popc(want)));
+                    limit = ka.counters->tail[level];
+                }
                 first = __shfl_sync(FULL, first, leader);
                 limit = __shfl_sync(FULL, limit, leader);
                 const unsigned int slot = first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
@@ -336,8 +357,8 @@ __global__ void k_affine_reject(KernelArgs ka, int queue) {
     }
 }
 
-#define LOGAN_AFFINE_LEVELS(X) X(0, 8, 8) X(1, 32, 8) X(2, 32, 16)
-constexpr int kAffineLevels = 3;
+#define LOGAN_AFFINE_LEVELS(X) X(0, 8, 8) X(1, 8, 16) X(2, 16, 16) X(3, 32, 16)
+constexpr int kAffineLevels = 4;
 
 }  // namespace
 
