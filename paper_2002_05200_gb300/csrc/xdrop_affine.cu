@@ -9,9 +9,11 @@
 //
 // Units of G lanes x C rows as in the linear kernels (lane g owns rows
 // base + g*C + k of a window that slides up in whole lanes), absolute
-// scores with -inf = NEGA, H on d-2 / d-1 / d and E, F on d-1 / d in
-// registers; the loop is unrolled six times so that the three H arrays and
-// the two E / F arrays all rotate roles without moves.  Keys
+// scores with -inf = NEGA.  H on d-2 / d-1 / d lives in three register
+// arrays that rotate roles (the loop is unrolled three times); E and F are
+// updated in place, rows in descending order: E(i,j) reads its own row on
+// d-1 and F(i,j) the row below, which is not yet overwritten.  (A six-step
+// unroll with two E / F arrays each stalled on instruction fetch.)  Keys
 // (H - T_d) * W + (W - 1 - row) give the best and its tie-break in one max.
 // Levels: 64 rows (8 lanes x 8, four extensions per warp), 128 (8 x 16,
 // four per warp), 256 (16 x 16, two per warp) and 512 (32 x 16); an item
@@ -35,7 +37,7 @@ struct AGroup {
     static constexpr uint32_t MASK2C = (C >= 16) ? 0xffffffffu : ((1u << (2 * C)) - 1u);
     static constexpr uint32_t ALLC = (C >= 32) ? 0xffffffffu : ((1u << C) - 1u);
     static constexpr int PREFETCH = 16 * G;  // b' codes held by a unit
-    static constexpr int UNROLL = 6;         // steps per loop iteration
+    static constexpr int UNROLL = 3;         // steps per loop iteration
     static_assert(C <= 16 && C % 2 == 0, "a lane's row codes fit one word");
     static_assert((1 << LOG2W) == W, "window must be a power of two");
 };
@@ -57,6 +59,7 @@ struct AState {
 template <int G, int C>
 __device__ __forceinline__ void a_init(const KernelArgs& ka, AState& u, uint32_t id, int gl,
                                        int (&H2)[C], int (&H1)[C], int (&E1)[C], int (&F1)[C]) {
+    // H2, H1: H on d-2, d-1; E1, F1: E, F on d-1
     const Item it = ka.items[id];
     u.item = id;
     u.apos = it.a_pos;
@@ -182,12 +185,11 @@ __device__ __forceinline__ int a_unit_max(int v) {
 }
 
 // One anti-diagonal of every unit of the warp: H2 = H on d-2, H1 = H on
-// d-1, E1/F1 = E/F on d-1; HO/EO/FO receive d.
+// d-1, HO receives H on d; EF: E and F on d-1, replaced by those of d.
 template <int G, int C>
 __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, AState& u, int gl,
                                        int unit, const int (&H2)[C], const int (&H1)[C],
-                                       const int (&E1)[C], const int (&F1)[C], int (&HO)[C],
-                                       int (&EO)[C], int (&FO)[C]) {
+                                       int (&HO)[C], int (&E)[C], int (&F)[C]) {
     using Gr = AGroup<G, C>;
     const int rlo = max(u.lo, u.d - u.n);
     const int rhi = min(u.hi + 1, u.m);
@@ -201,7 +203,7 @@ __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, ASt
     u.bw = ((u.bw << 2) | carry) & Gr::MASK2C;
     // the row below the lane: H and F on d-1 (for F), H on d-2 (diagonal)
     int h1c = __shfl_up_sync(FULL, H1[C - 1], 1, G);
-    int f1c = __shfl_up_sync(FULL, F1[C - 1], 1, G);
+    int f1c = __shfl_up_sync(FULL, F[C - 1], 1, G);
     int h2c = __shfl_up_sync(FULL, H2[C - 1], 1, G);
     if (gl == 0) h1c = f1c = h2c = NEGA;
     const uint32_t x = u.aw ^ u.bw;
@@ -223,25 +225,25 @@ __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, ASt
     const uint32_t kbase = uint32_t(C - 1) - uint32_t(T) * uint32_t(Gr::W);
     const uint32_t wscale = uint32_t(one) * uint32_t(Gr::W);
     int lkey = -1;
-    uint32_t bits = 0u;  // bit C-1-k: row k live
+    uint32_t bits = 0u;  // bit k: row k live
 #pragma unroll
-    for (int k = 0; k < C; k += 2) {
+    for (int k = C - 2; k >= 0; k -= 2) {
         int key[2];
 #pragma unroll
-        for (int hh = 0; hh < 2; ++hh) {
-            const int kk = k + hh;
+        for (int hh = 1; hh >= 0; --hh) {
+            const int kk = k + hh;  // descending: F[kk-1] still holds d-1
             const int uh = kk ? H1[kk - 1] : h1c;
-            const int uf = kk ? F1[kk - 1] : f1c;
+            const int uf = kk ? F[kk - 1] : f1c;
             const int dg = kk ? H2[kk - 1] : h2c;
-            const int e = __vimax3_s32(E1[kk] * one + ge, H1[kk] * one + goe, NEGA);
+            const int e = __vimax3_s32(E[kk] * one + ge, H1[kk] * one + goe, NEGA);
             const int f = __vimax3_s32(uf * one + ge, uh * one + goe, NEGA);
             const int y = __mulhi(int(eq * ka.pw[kk]), one);  // -1 on a match, else 0
             const int t = y * dsub + (dg * one + ka.sc.mismatch);
             const int h = __vimax3_s32(t, e, f);
             const bool live = ((rb >> kk) & 1u) && h >= T;
             HO[kk] = live ? h : NEGA;
-            EO[kk] = live ? e : NEGA;
-            FO[kk] = live ? f : NEGA;
+            E[kk] = live ? e : NEGA;
+            F[kk] = live ? f : NEGA;
             // live: 0 <= h - T <= X + match, so the key stays below 2^31
             key[hh] = live ? int(uint32_t(h) * wscale + (kbase - uint32_t(kk))) : -1;
             bits = (bits << 1) | (live ? 1u : 0u);
@@ -252,16 +254,16 @@ __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, ASt
     const int wkey = a_unit_max<G>(lkey >= 0 ? lkey + (G - 1 - gl) * C : -1);
     int rfirst, rlast;
     if constexpr (G == 32) {
-        rfirst = __reduce_min_sync(FULL, bits ? gl * C + (__clz(bits) - (32 - C)) : Gr::W);
-        rlast = __reduce_max_sync(FULL, bits ? gl * C + (C - __ffs(bits)) : -1);
+        rfirst = __reduce_min_sync(FULL, bits ? gl * C + (__ffs(bits) - 1) : Gr::W);
+        rlast = __reduce_max_sync(FULL, bits ? gl * C + (31 - __clz(bits)) : -1);
     } else {
         const uint32_t vote = __ballot_sync(FULL, bits != 0u);
         const uint32_t uvv = (vote >> (unit * G)) & ((1u << G) - 1u);
         const int fl = uvv ? __ffs(uvv) - 1 : 0, ll = uvv ? 31 - __clz(uvv) : 0;
         const uint32_t fb = __shfl_sync(FULL, bits, unit * G + fl);
         const uint32_t lb = __shfl_sync(FULL, bits, unit * G + ll);
-        rfirst = uvv ? fl * C + (__clz(fb) - (32 - C)) : Gr::W;
-        rlast = uvv ? ll * C + (C - __ffs(lb)) : -1;
+        rfirst = uvv ? fl * C + (__ffs(fb) - 1) : Gr::W;
+        rlast = uvv ? ll * C + (31 - __clz(lb)) : -1;
     }
     if (run && rlast >= 0) {
         const int hmax = T + (wkey >> Gr::LOG2W);
@@ -280,14 +282,14 @@ __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, ASt
 }
 
 template <int G, int C>
-__global__ void __launch_bounds__(128, (C == 16) ? 3 : 4) k_affine(KernelArgs ka, int go, int ge, int level,
+__global__ void __launch_bounds__(128, 4) k_affine(KernelArgs ka, int go, int ge, int level,
                                                 int n_levels) {
     const int lane = threadIdx.x & 31;
     const int gl = lane % G, unit = lane / G;
     const uint32_t* q = ka.queues + size_t(level) * ka.qcap;
-    int P0[C], P1[C], P2[C], E0[C], E1[C], F0[C], F1[C];
+    int P0[C], P1[C], P2[C], E[C], F[C];
 #pragma unroll
-    for (int k = 0; k < C; ++k) P0[k] = P1[k] = P2[k] = E0[k] = E1[k] = F0[k] = F1[k] = NEGA;
+    for (int k = 0; k < C; ++k) P0[k] = P1[k] = P2[k] = E[k] = F[k] = NEGA;
     AState u;
     u.active = u.done = u.overflow = false;
     u.item = 0u;
@@ -326,20 +328,17 @@ __global__ void __launch_bounds__(128, (C == 16) ? 3 : 4) k_affine(KernelArgs ka
                 if (need && slot < limit) id = q[slot];
             }
             if (need) {
-                // the roles are P1 = d-1, P0 = d-2, E0/F0 = d-1 at the loop top
-                if (id != 0xffffffffu) a_init<G, C>(ka, u, id, gl, P0, P1, E0, F0);
+                // the roles are P0 = d-2, P1 = d-1 at the loop top
+                if (id != 0xffffffffu) a_init<G, C>(ka, u, id, gl, P0, P1, E, F);
                 else exhausted = true;
             }
         }
         if (!__any_sync(FULL, u.active)) break;
-        a_prepare<G, C>(ka, u, gl, P0, P1, E0, F0);
-        a_step<G, C>(ka, go, ge, u, gl, unit, P0, P1, E0, F0, P2, E1, F1);
-        a_step<G, C>(ka, go, ge, u, gl, unit, P1, P2, E1, F1, P0, E0, F0);
-        a_step<G, C>(ka, go, ge, u, gl, unit, P2, P0, E0, F0, P1, E1, F1);
-        a_step<G, C>(ka, go, ge, u, gl, unit, P0, P1, E1, F1, P2, E0, F0);
-        a_step<G, C>(ka, go, ge, u, gl, unit, P1, P2, E0, F0, P0, E1, F1);
-        a_step<G, C>(ka, go, ge, u, gl, unit, P2, P0, E1, F1, P1, E0, F0);
-        // roles are back to P0 = d-2, P1 = d-1, E0/F0 = d-1
+        a_prepare<G, C>(ka, u, gl, P0, P1, E, F);
+        a_step<G, C>(ka, go, ge, u, gl, unit, P0, P1, P2, E, F);
+        a_step<G, C>(ka, go, ge, u, gl, unit, P1, P2, P0, E, F);
+        a_step<G, C>(ka, go, ge, u, gl, unit, P2, P0, P1, E, F);
+        // roles are back to P0 = d-2, P1 = d-1
     }
 }
 
