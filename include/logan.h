@@ -152,9 +152,10 @@ int logan_extend_batch(logan_ctx_t *ctx, const logan_seqs_t *seqsA, const logan_
                        logan_result_t *out, void *stream);
 
 /* Same operation and results, one-launch-per-batch baseline form (the
- * paper's Sec. IV-B inter-sequence scheme): one warp per extension in input
- * order, no binning and no persistence; bands that outgrow its window go to
- * the same wider fallbacks. */
+ * paper's Sec. IV-B inter-sequence scheme): one unit per extension in input
+ * order at the level LOGAN_OPT_PLAIN_LEVEL (default the 64-row level), no
+ * binning and no persistence; bands that outgrow its window go to the same
+ * wider levels and fallback. */
 int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                              const logan_seqs_t *seqsB, const logan_seed_t *seeds,
                              uint32_t n_pairs, int32_t match, int32_t mismatch, int32_t gap,
