@@ -193,6 +193,72 @@ int logan_extend_batch_affine(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                               const int32_t *X_per_pair, void *workspace, size_t ws_bytes,
                               logan_result_t *out, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Many-to-many overlap seeding (the step before extension in the paper's
+ * application, Sec. V: k-mers as seeds, pruning of k-mers unlikely to be
+ * useful, a seed per overlapping pair chosen from the k-mer locations, and
+ * an adaptive threshold on the extension score).  The paper describes these
+ * steps in words only; the definitions below are this library's.
+ *
+ * K-mer codes: base codes A0 C1 G2 T3; the forward code of the k-mer at
+ * position p of a read is sum_t c[p+t] << 2t (t < k), the reverse-complement
+ * code sum_t (3 - c[p+k-1-t]) << 2t; the canonical code is the smaller, the
+ * occurrence's strand 1 when the reverse complement is strictly smaller.
+ * A k-mer is reliable when min_freq <= (occurrences over all reads) <=
+ * max_freq.  Two occurrences of a reliable k-mer in reads a < b are a hit
+ * (a, b, o = strand_a xor strand_b, pos_a, pos_b).  A candidate is an
+ * (a, b, o) with at least min_shared hits; its seed is the hit at index
+ * count / 2 in (pos_a, pos_b) order (the middle of the chain).
+ */
+typedef struct {
+    uint32_t a, b;        /* read indices, a < b */
+    uint32_t o;           /* 1: read b's reverse complement overlaps read a */
+    uint32_t pos_a;       /* seed k-mer start in read a */
+    uint32_t pos_b;       /* seed k-mer start in read b (forward strand) */
+    uint32_t count;       /* hits of the pair */
+} logan_candidate_t;
+
+/* Candidates of the packed read pool `reads` (device, packed2bit = 1),
+ * in (a, b, o) order, written to out (device, up to `capacity`); *n_found
+ * (host) receives the number found (possibly above capacity).  1 <= k <= 31,
+ * 2 <= min_freq <= max_freq <= 1024, min_shared >= 1.  Temporary memory is
+ * taken from the device's stream-ordered pool (cudaMallocAsync) and returned
+ * before the call ends; the call synchronises `stream`.  Returns
+ * LOGAN_EINVAL for invalid arguments, LOGAN_ENOMEM when a temporary buffer
+ * cannot be had, LOGAN_ECUDA on a CUDA failure. */
+int logan_overlap_candidates(logan_ctx_t *ctx, const logan_seqs_t *reads, int k,
+                             uint32_t min_freq, uint32_t max_freq, uint32_t min_shared,
+                             logan_candidate_t *out, uint64_t capacity, uint64_t *n_found,
+                             void *stream);
+
+/* Words needed by logan_overlap_pool for `reads` (synchronises `stream`). */
+int logan_overlap_pool_words(logan_ctx_t *ctx, const logan_seqs_t *reads, uint64_t *words,
+                             void *stream);
+
+/* The pool the B side of the extension reads: sequences 0 .. R-1 are the
+ * reads, R + r the reverse complement of read r (packed, 16-base aligned
+ * after the reads' words).  words_out: device, >= logan_overlap_pool_words;
+ * offsets_out, lengths_out: device, 2R entries; *pool_out describes the
+ * result.  Synchronises `stream`. */
+int logan_overlap_pool(logan_ctx_t *ctx, const logan_seqs_t *reads, uint32_t *words_out,
+                       uint64_t words_capacity, uint64_t *offsets_out, uint32_t *lengths_out,
+                       logan_seqs_t *pool_out, void *stream);
+
+/* Extension seeds of n candidates (device): A = read a at pos_a; B = read b
+ * at pos_b (o = 0) or its reverse complement, sequence R + b of the
+ * logan_overlap_pool, at len_b - pos_b - k (o = 1); seed length k. */
+int logan_overlap_seeds(logan_ctx_t *ctx, const logan_candidate_t *cands, uint64_t n,
+                        const logan_seqs_t *reads, int k, logan_seed_t *seeds, void *stream);
+
+/* Adaptive threshold on n extension results (device): keep[i] = 1 when
+ * results[i].status == LOGAN_OK and score * den >= ratio_num * L - delta * den,
+ * with L = min(posA, posB) + k + min(lenA - posA - k, lenB - posB - k) the
+ * overlap the seed's diagonal implies (lengths from seqsA / seqsB). */
+int logan_overlap_keep(logan_ctx_t *ctx, const logan_result_t *results,
+                       const logan_seed_t *seeds, uint64_t n, const logan_seqs_t *seqsA,
+                       const logan_seqs_t *seqsB, int64_t ratio_num, int64_t den, int64_t delta,
+                       uint8_t *keep, void *stream);
+
 /*
  * Same operation and results as logan_extend_batch, for callers that cannot
  * allocate device memory -- e.g. a host whose GPU memory is owned by another

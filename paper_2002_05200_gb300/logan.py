@@ -31,7 +31,8 @@ assert RESULT_DTYPE.itemsize == 40
 
 EXPORTED = ["logan_version", "logan_strerror", "logan_ctx_create", "logan_ctx_destroy",
             "logan_workspace_size", "logan_extend_batch", "logan_extend_batch_plain",
-            "logan_extend_batch_affine",
+            "logan_extend_batch_affine", "logan_overlap_candidates", "logan_overlap_pool_words",
+            "logan_overlap_pool", "logan_overlap_seeds", "logan_overlap_keep",
             "logan_set_option", "logan_get_option", "logan_num_levels", "logan_level_info",
             "logan_last_stats", "logan_call_stats", "logan_set_level_table",
             "logan_get_level_table", "logan_intpeak", "logan_autotune", "logan_autotune_save",
@@ -102,6 +103,15 @@ def lib():
         L.logan_extend_batch.argtypes = ext_args
         L.logan_extend_batch_plain.argtypes = ext_args
         L.logan_extend_batch_affine.argtypes = ext_args[:7] + [ctypes.c_int32] + ext_args[7:]
+        u64 = ctypes.c_uint64
+        L.logan_overlap_candidates.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.c_int, u32, u32, u32,
+                                               p, u64, ctypes.POINTER(u64), p]
+        L.logan_overlap_pool_words.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.POINTER(u64), p]
+        L.logan_overlap_pool.argtypes = [p, ctypes.POINTER(SeqsT), p, u64, p, p,
+                                         ctypes.POINTER(SeqsT), p]
+        L.logan_overlap_seeds.argtypes = [p, p, u64, ctypes.POINTER(SeqsT), ctypes.c_int, p, p]
+        L.logan_overlap_keep.argtypes = [p, p, p, u64, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT),
+                                         ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, p, p]
         L.logan_set_option.argtypes = [p, ctypes.c_int, i64]
         L.logan_get_option.argtypes = [p, ctypes.c_int, ctypes.POINTER(i64)]
         L.logan_level_info.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -333,6 +343,78 @@ class Context:
             workspace.numel(), out.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
         _check(rc, "logan_extend_batch_affine")
         return out[:n]
+
+    # ---- many-to-many overlap seeding (logan_overlap_*) ----
+
+    def overlap_candidates(self, reads: DevicePool, k: int = 17, min_freq: int = 2,
+                           max_freq: int = 4, min_shared: int = 1, stream=None):
+        """Candidates (int32 view of uint32 [n, 6]: a, b, o, pos_a, pos_b, count)
+        of a packed read pool, in (a, b, o) order."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        n = ctypes.c_uint64()
+        cr = reads.c()
+        args = (self._h, ctypes.byref(cr), k, min_freq, max_freq, min_shared)
+        _check(lib().logan_overlap_candidates(*args, None, 0, ctypes.byref(n),
+                                              ctypes.c_void_p(stream.cuda_stream)),
+               "logan_overlap_candidates")
+        out = torch.empty((max(n.value, 1), 6), dtype=torch.int32, device=f"cuda:{self.device}")
+        if n.value:
+            _check(lib().logan_overlap_candidates(*args, out.data_ptr(), n.value, ctypes.byref(n),
+                                                  ctypes.c_void_p(stream.cuda_stream)),
+                   "logan_overlap_candidates")
+        return out[:n.value]
+
+    def overlap_pool(self, reads: DevicePool, stream=None) -> DevicePool:
+        """Reads followed by their reverse complements (the extension's B side)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        st = ctypes.c_void_p(stream.cuda_stream)
+        cr = reads.c()
+        w = ctypes.c_uint64()
+        _check(lib().logan_overlap_pool_words(self._h, ctypes.byref(cr), ctypes.byref(w), st),
+               "logan_overlap_pool_words")
+        dev = f"cuda:{self.device}"
+        words = torch.empty(w.value, dtype=torch.int32, device=dev)
+        off = torch.empty(max(2 * reads.count, 1), dtype=torch.int64, device=dev)
+        ln = torch.empty(max(2 * reads.count, 1), dtype=torch.int32, device=dev)
+        po = SeqsT()
+        _check(lib().logan_overlap_pool(self._h, ctypes.byref(cr), words.data_ptr(), w.value,
+                                        off.data_ptr(), ln.data_ptr(), ctypes.byref(po), st),
+               "logan_overlap_pool")
+        return DevicePool(words, off[:2 * reads.count], ln[:2 * reads.count], True, po.pool_bases)
+
+    def overlap_seeds(self, cands, reads: DevicePool, k: int = 17, stream=None):
+        """Extension seeds (int32 [n, 5]) of candidates, B = overlap_pool(reads)."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        n = int(cands.shape[0])
+        seeds = torch.empty((max(n, 1), 5), dtype=torch.int32, device=f"cuda:{self.device}")
+        cr = reads.c()
+        _check(lib().logan_overlap_seeds(self._h, cands.data_ptr() if n else None, n,
+                                         ctypes.byref(cr), k, seeds.data_ptr(),
+                                         ctypes.c_void_p(stream.cuda_stream)),
+               "logan_overlap_seeds")
+        return seeds[:n]
+
+    def overlap_keep(self, results, seeds, A: DevicePool, B: DevicePool, ratio_num: int,
+                     den: int, delta: int, stream=None):
+        """Adaptive-threshold decisions (uint8 [n]) of extension results."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        n = int(seeds.shape[0])
+        keep = torch.empty(max(n, 1), dtype=torch.uint8, device=f"cuda:{self.device}")
+        ca, cb = A.c(), B.c()
+        _check(lib().logan_overlap_keep(self._h, results.data_ptr() if n else None,
+                                        seeds.data_ptr() if n else None, n, ctypes.byref(ca),
+                                        ctypes.byref(cb), ratio_num, den, delta, keep.data_ptr(),
+                                        ctypes.c_void_p(stream.cuda_stream)),
+               "logan_overlap_keep")
+        return keep[:n]
 
     def last_stats(self, back: int = 0) -> dict:
         """Per-level device ms / items / completed cells of a call made with
