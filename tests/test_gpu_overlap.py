@@ -89,3 +89,40 @@ def test_pool_seeds_extension_and_threshold(ctx):
                     want["posB"], k, 1, 4, 20)
     assert np.array_equal(keep.cpu().numpy().astype(bool), k_ref)
     assert 0 < k_ref.sum() < k_ref.size
+
+
+def test_full_read_set_properties(ctx):
+    # the overlap workload's 50,000 reads (50 Mbp genome): candidates are
+    # unique, ordered, above the hit minimum, their seed k-mers agree, and
+    # every pair of reads sharing >= 4 kbp of genome on the same strand
+    # relation is found
+    k, mshared = 17, 4
+    b = synth.overlap_batch(n_pairs=1000)
+    R = b.meta["n_reads"]
+    idx = np.arange(0, 2 * R, 2)
+    A = logan.pool_to_device(b.poolA, b.offA[idx].copy(), b.lenA[idx].copy(), True,
+                             (b.poolA.size - 1) * 16)
+    c = ctx.overlap_candidates(A, k, 2, 4, mshared).cpu().numpy().view(np.uint32)
+    a_, b_, o_ = c[:, 0].astype(np.int64), c[:, 1].astype(np.int64), c[:, 2].astype(np.int64)
+    key = (a_ << 33) | (b_ << 1) | o_
+    assert np.all(a_ < b_) and np.all(np.diff(key) > 0) and np.all(c[:, 5] >= mshared)
+    rng = np.random.default_rng(301)
+    reads = lambda i: b._seq(b.poolA, b.offA, b.lenA, 2 * int(i))
+    for j in rng.choice(c.shape[0], 500, replace=False):
+        sa = reads(c[j, 0])[c[j, 3]:c[j, 3] + k]
+        sb = reads(c[j, 1])[c[j, 4]:c[j, 4] + k]
+        assert sa == (ov.revcomp(sb) if c[j, 2] else sb)
+    rs, rl, rv = b.meta["read_start"], b.meta["read_len"], b.meta["read_rev"]
+    found = set(zip(a_.tolist(), b_.tolist(), o_.tolist()))
+    order = np.argsort(rs, kind="stable")
+    missed = checked = 0
+    for i in rng.choice(R, 2000, replace=False):
+        lo = np.searchsorted(rs[order], rs[i], side="left")
+        hi = np.searchsorted(rs[order], rs[i] + rl[i] - 4000, side="left")
+        for j in order[lo:hi]:
+            if j == i or min(rs[i] + rl[i], rs[j] + rl[j]) - max(rs[i], rs[j]) < 4000:
+                continue
+            p, q = (i, j) if i < j else (j, i)
+            checked += 1
+            missed += (p, q, int(rv[i] ^ rv[j])) not in found
+    assert checked > 1000 and missed <= checked // 100
