@@ -24,6 +24,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "xdrop_oracle.c")
 _SRC_AFFINE = os.path.join(_HERE, "xdrop_affine_oracle.c")
+_SRC_TRACE = os.path.join(_HERE, "xdrop_traceback_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
@@ -44,10 +45,11 @@ def build(force: bool = False) -> str:
     os.makedirs(_BUILD, exist_ok=True)
     if force or not os.path.exists(_LIB_PATH) or \
             os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
-                                              os.path.getmtime(_SRC_AFFINE)):
+                                              os.path.getmtime(_SRC_AFFINE),
+                                              os.path.getmtime(_SRC_TRACE)):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC, _SRC_AFFINE])
+                               "-o", tmp, _SRC, _SRC_AFFINE, _SRC_TRACE])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -81,6 +83,13 @@ def lib():
         L.oracle_affine_batch.restype = ctypes.c_int
         L.oracle_affine_params_valid.argtypes = [i64, i64, i64, i64, i64]
         L.oracle_affine_params_valid.restype = ctypes.c_int
+        pi64 = ctypes.POINTER(i64)
+        L.oracle_xdrop_traceback.argtypes = [p, i64, p, i64, i64, i64, i64, i64, pi64, pi64, pi64,
+                                             pi64, p, pi64]
+        L.oracle_xdrop_traceback.restype = ctypes.c_int
+        L.oracle_pair_traceback.argtypes = [p, i64, p, i64, i64, i64, i64, i64, i64, i64, i64, p,
+                                            pi64]
+        L.oracle_pair_traceback.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -212,3 +221,31 @@ def run_batch_affine(b, gap_open: int, gap_extend: int, threads: Optional[int] =
                                      None if xs is None else xs.ctypes.data, int(threads),
                                      out.ctypes.data)
     return out, used
+
+
+# ---- alignment paths (xdrop_traceback_oracle.c) ----
+
+def traceback(a: bytes, b: bytes, match: int = 1, mismatch: int = -1, gap: int = -1,
+              X: int = 50):
+    """One extension with its path: (best, bi, bj, cells, ops) where ops is a
+    string of 'M' / 'I' / 'D' from (0,0) to the best cell."""
+    v = [ctypes.c_int64() for _ in range(5)]
+    buf = ctypes.create_string_buffer(len(a) + len(b) + 1)
+    rc = lib().oracle_xdrop_traceback(_buf(a), len(a), _buf(b), len(b), match, mismatch, gap, X,
+                                      *[ctypes.byref(x) for x in v[:4]], buf, ctypes.byref(v[4]))
+    if rc:
+        raise MemoryError("oracle traceback could not allocate")
+    return v[0].value, v[1].value, v[2].value, v[3].value, buf.raw[:v[4].value].decode()
+
+
+def pair_traceback(A: bytes, B: bytes, posA: int, posB: int, k: int, match: int = 1,
+                   mismatch: int = -1, gap: int = -1, X: int = 50) -> str:
+    """A seeded pair's alignment as 'M' / 'I' / 'D' operations from
+    (begA, begB) to (endA, endB)."""
+    n = ctypes.c_int64()
+    buf = ctypes.create_string_buffer(len(A) + len(B) + 1)
+    rc = lib().oracle_pair_traceback(_buf(A), len(A), _buf(B), len(B), posA, posB, k, match,
+                                     mismatch, gap, X, buf, ctypes.byref(n))
+    if rc:
+        raise ValueError("invalid pair or allocation failure")
+    return buf.raw[:n.value].decode()
