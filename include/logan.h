@@ -259,6 +259,37 @@ int logan_overlap_keep(logan_ctx_t *ctx, const logan_result_t *results,
                        const logan_seqs_t *seqsB, int64_t ratio_num, int64_t den, int64_t delta,
                        uint8_t *keep, void *stream);
 
+/* ---------------------------------------------------------------------------
+ * Alignment paths (the paper keeps no traceback, Sec. IV-A).
+ *
+ * For every pair the path of its reported alignment: each live cell keeps
+ * the predecessor term that gave its score (the diagonal first, then the
+ * vertical move (i-1, j), then the horizontal one (i, j-1)); a side's path
+ * is the walk from its best cell back to (0,0); a pair's alignment is the
+ * left path in the sequences' order, k matches/mismatches for the seed, then
+ * the right path, spanning [begA, endA) x [begB, endB) of logan_extend_batch's
+ * result.  Operations are run-length codes (length << 4 | op) with op
+ * 0 = M (a diagonal step: match or mismatch), 1 = I (a base of A only),
+ * 2 = D (a base of B only) -- the BAM encoding of these three.
+ *   Arguments as logan_extend_batch (pools may be ASCII or packed; device).
+ *   ops: device uint32 codes; pair p's codes are ops[op_start[p] ..
+ *   op_start[p] + op_count[p]) (op_start: device uint64[n_pairs],
+ *   op_count: device uint32[n_pairs]; 0 codes for an invalid pair or one
+ *   whose band outgrows the fallback ring).  *ops_needed (host) receives the
+ *   codes the batch needs; with ops_capacity below it the call returns
+ *   LOGAN_ENOMEM after sizing (call again with more).
+ * Work: each extension is swept twice by a block in device memory (once to
+ * its end, once up to its best anti-diagonal recording 2-bit predecessor
+ * codes) -- meant for the pairs a caller keeps, not whole raw batches.
+ * Temporary memory comes from the stream-ordered pool (cudaMallocAsync); the
+ * call synchronises `stream`. */
+int logan_traceback_batch(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
+                          const logan_seqs_t *seqsB, const logan_seed_t *seeds,
+                          uint32_t n_pairs, int32_t match, int32_t mismatch, int32_t gap,
+                          int32_t X, const int32_t *X_per_pair, uint32_t *ops,
+                          uint64_t ops_capacity, uint64_t *op_start, uint32_t *op_count,
+                          uint64_t *ops_needed, void *stream);
+
 /*
  * Same operation and results as logan_extend_batch, for callers that cannot
  * allocate device memory -- e.g. a host whose GPU memory is owned by another

@@ -33,6 +33,7 @@ EXPORTED = ["logan_version", "logan_strerror", "logan_ctx_create", "logan_ctx_de
             "logan_workspace_size", "logan_extend_batch", "logan_extend_batch_plain",
             "logan_extend_batch_affine", "logan_overlap_candidates", "logan_overlap_pool_words",
             "logan_overlap_pool", "logan_overlap_seeds", "logan_overlap_keep",
+            "logan_traceback_batch",
             "logan_set_option", "logan_get_option", "logan_num_levels", "logan_level_info",
             "logan_last_stats", "logan_call_stats", "logan_set_level_table",
             "logan_get_level_table", "logan_intpeak", "logan_autotune", "logan_autotune_save",
@@ -112,6 +113,9 @@ def lib():
         L.logan_overlap_seeds.argtypes = [p, p, u64, ctypes.POINTER(SeqsT), ctypes.c_int, p, p]
         L.logan_overlap_keep.argtypes = [p, p, p, u64, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT),
                                          ctypes.c_int64, ctypes.c_int64, ctypes.c_int64, p, p]
+        L.logan_traceback_batch.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT), p, u32,
+                                            i32, i32, i32, i32, p, p, u64, p, p,
+                                            ctypes.POINTER(u64), p]
         L.logan_set_option.argtypes = [p, ctypes.c_int, i64]
         L.logan_get_option.argtypes = [p, ctypes.c_int, ctypes.POINTER(i64)]
         L.logan_level_info.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -343,6 +347,36 @@ class Context:
             workspace.numel(), out.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
         _check(rc, "logan_extend_batch_affine")
         return out[:n]
+
+    def traceback(self, A: DevicePool, B: DevicePool, seeds, match: int = 1, mismatch: int = -1,
+                  gap: int = -1, X: int = 50, X_per_pair=None, stream=None):
+        """Alignment paths (logan_traceback_batch): (codes int32 [total],
+        op_start int64 [n], op_count int32 [n]); code = length << 4 | op,
+        op 0 = M, 1 = I, 2 = D."""
+        import torch
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        n = int(seeds.shape[0])
+        dev = f"cuda:{self.device}"
+        start = torch.empty(max(n, 1), dtype=torch.int64, device=dev)
+        count = torch.empty(max(n, 1), dtype=torch.int32, device=dev)
+        ca, cb = A.c(), B.c()
+        need = ctypes.c_uint64()
+
+        def call(buf, cap):
+            return lib().logan_traceback_batch(
+                self._h, ctypes.byref(ca), ctypes.byref(cb), seeds.data_ptr() if n else None, n,
+                match, mismatch, gap, X,
+                X_per_pair.data_ptr() if X_per_pair is not None else None,
+                buf.data_ptr() if buf is not None else None, cap, start.data_ptr(),
+                count.data_ptr(), ctypes.byref(need), ctypes.c_void_p(stream.cuda_stream))
+        rc = call(None, 0)
+        if rc not in (OK, ENOMEM) or (rc == ENOMEM and need.value == 0):
+            _check(rc, "logan_traceback_batch")
+        codes = torch.empty(max(need.value, 1), dtype=torch.int32, device=dev)
+        if need.value:
+            _check(call(codes, need.value), "logan_traceback_batch")
+        return codes, start[:n], count[:n]
 
     # ---- many-to-many overlap seeding (logan_overlap_*) ----
 

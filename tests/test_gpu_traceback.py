@@ -1,0 +1,109 @@
+"""Alignment paths on the GPU (logan_traceback_batch) vs the traceback
+oracle: every pair's run-length operations exactly; the paths span the
+extension's reported coordinates and rescore to its score."""
+import numpy as np
+import pytest
+
+import oracle
+from paper_2002_05200_gb300 import logan, synth
+
+pytestmark = pytest.mark.gpu
+
+OPS = "MID"
+
+
+@pytest.fixture(scope="module")
+def ctx():
+    import torch
+    if not torch.cuda.is_available():
+        pytest.skip("no GPU")
+    c = logan.Context(0)
+    yield c
+    c.close()
+
+
+def rle(ops: str):
+    out = []
+    for o in ops:
+        code = OPS.index(o)
+        if out and (out[-1] & 15) == code:
+            out[-1] += 16
+        else:
+            out.append(16 | code)
+    return out
+
+
+def gpu_paths(ctx, b, packed2bit=False):
+    import torch
+    A, B, S, Xs = logan.batch_to_device(b, packed2bit=packed2bit)
+    codes, start, count = ctx.traceback(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs)
+    res = ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs)
+    torch.cuda.synchronize()
+    c = codes.cpu().numpy().view(np.uint32)
+    st, ct = start.cpu().numpy(), count.cpu().numpy()
+    return [list(c[st[p]:st[p] + ct[p]]) for p in range(b.n_pairs)], logan.results_to_numpy(res)
+
+
+def check(b, paths, res, Xs=None):
+    for p in range(b.n_pairs):
+        s = b.seeds[p]
+        if res["status"][p] != 0:
+            assert paths[p] == []
+            continue
+        X = int(b.Xs[p]) if b.Xs is not None else b.X
+        want = oracle.pair_traceback(b.seqA(p), b.seqB(p), int(s["posA"]), int(s["posB"]),
+                                     int(s["len"]), b.match, b.mismatch, b.gap, X)
+        assert [int(x) for x in paths[p]] == rle(want), p
+        # the path spans the reported coordinates and rescores to the score
+        A, B = b.seqA(p), b.seqB(p)
+        i, j, sc = int(res["begA"][p]), int(res["begB"][p]), 0
+        for code in paths[p]:
+            op, n = int(code) & 15, int(code) >> 4
+            for _ in range(n):
+                if op == 0:
+                    sc += b.match if A[i] == B[j] else b.mismatch
+                    i += 1; j += 1
+                elif op == 1:
+                    sc += b.gap; i += 1
+                else:
+                    sc += b.gap; j += 1
+        assert (i, j, sc) == (int(res["endA"][p]), int(res["endB"][p]), int(res["score"][p]))
+
+
+def test_uniform_pairs(ctx):
+    b = synth.uniform_pairs(n_pairs=200)
+    check(b, *gpu_paths(ctx, b))
+
+
+def test_lognormal_packed(ctx):
+    b = synth.lognormal_batch(n_pairs=120)
+    check(b, *gpu_paths(ctx, b, packed2bit=True))
+
+
+def test_uneven_per_pair_x(ctx):
+    b = synth.uneven_batch(n_pairs=80, max_len=15_000, seed=81)
+    check(b, *gpu_paths(ctx, b, packed2bit=True))
+
+
+@pytest.mark.parametrize("seed", range(2))
+def test_tiny_edge_cases(ctx, seed):
+    b = synth.tiny_pairs(2000, 40, seed=seed)
+    check(b, *gpu_paths(ctx, b))
+
+
+@pytest.mark.parametrize("scheme", [(2, -3, -2), (1, -1, 0), (5, -4, -7)])
+def test_scoring_schemes(ctx, scheme):
+    b = synth.uniform_pairs(n_pairs=60)
+    b.match, b.mismatch, b.gap = scheme
+    check(b, *gpu_paths(ctx, b))
+
+
+def test_invalid_pairs_have_no_path(ctx):
+    b = synth.uniform_pairs(n_pairs=30)
+    pool = b.poolA.copy()
+    pool[::97] = ord("N")
+    b.poolA = pool
+    paths, res = gpu_paths(ctx, b)
+    bad = res["status"] != 0
+    assert bad.any() and all(paths[p] == [] for p in np.flatnonzero(bad))
+    check(b, paths, res)
