@@ -79,6 +79,9 @@ def parse():
                     help="affine gaps: time logan_extend_batch_affine with this gap_open "
                          "(and --gap-extend) instead of the linear path")
     ap.add_argument("--gap-extend", type=int, default=-1)
+    ap.add_argument("--traceback", type=int, default=0,
+                    help="time logan_traceback_batch on the first N pairs of the workload "
+                         "instead (alignment paths)")
     ap.add_argument("--concurrent", type=int, default=1, choices=[0, 1],
                     help="1: the start levels of a batch run concurrently (default); "
                          "0: level after level on one stream")
@@ -335,6 +338,61 @@ def run_reference(args, rank, world):
 
 
 # ---------------------------------------------------------------- GPU arm
+def traceback_main(args, b, ctx, stream, rank, world, local, packed):
+    """Alignment paths of the first N pairs of the workload: time of
+    logan_traceback_batch (two sweeps per extension + the walks), paths
+    checked against the extension's coordinates; one JSON line."""
+    import torch
+
+    from paper_2002_05200_gb300 import logan
+    sub = b.subset(np.arange(min(args.traceback, b.n_pairs)))
+    A, B, S, Xs = logan.batch_to_device(sub, packed2bit=packed, device=f"cuda:{local}")
+    res = ctx.extend(A, B, S, sub.match, sub.mismatch, sub.gap, sub.X, Xs, stream=stream)
+    stream.synchronize()
+    r = logan.results_to_numpy(res)
+    for _ in range(max(1, args.warmup)):
+        with torch.cuda.stream(stream):
+            ctx.traceback(A, B, S, sub.match, sub.mismatch, sub.gap, sub.X, Xs, stream=stream)
+    torch.cuda.synchronize()
+    with ClockSampler(local) as clk:
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        for _ in range(args.steps):
+            with torch.cuda.stream(stream):
+                codes, start, count = ctx.traceback(A, B, S, sub.match, sub.mismatch, sub.gap,
+                                                    sub.X, Xs, stream=stream)
+        e1.record(stream)
+        e1.synchronize()
+    ms = e0.elapsed_time(e1) / args.steps
+    c = codes.cpu().numpy().view(np.uint32)
+    st, ct = start.cpu().numpy(), count.cpu().numpy()
+    span_ok = True
+    for p in range(sub.n_pairs):  # every path spans the pair's alignment
+        if r["status"][p]:
+            continue
+        cc = c[st[p]:st[p] + ct[p]]
+        n = cc >> 4
+        op = cc & 15
+        di = int(n[op != 2].sum())
+        dj = int(n[op != 1].sum())
+        span_ok &= (di, dj) == (int(r["endA"][p] - r["begA"][p]), int(r["endB"][p] - r["begB"][p]))
+    cells = int(r["cells"][r["status"] == 0].sum())
+    line = {"metric": METRIC + " -- alignment paths (logan_traceback_batch)",
+            "value": sub.n_pairs / (ms * 1e-3), "unit": "paths/s", "n_gpus": world,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
+            "data": "synthetic",
+            "config": dict(workload_config(b, args.workload, args.pairs), traced_pairs=sub.n_pairs),
+            "clocks": clk.summary(), "extension_cells": cells,
+            "gcups_equiv": cells / (ms * 1e-3) / 1e9,
+            "codes": int(ct.sum()), "paths_span_alignments": bool(span_ok),
+            "roofline": None,
+            "roofline_note": "two block-per-extension sweeps in device memory (the fallback "
+                             "kernel's layout) plus a walk per pair"}
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+
+
 def affine_main(args, b, A, B, S, Xs, ctx, ws, out, stream, timed, rank, world, local, packed):
     """The affine-gap path on the same workload: persistent time, e2e and the
     affine oracle on the host cores; one JSON line."""
@@ -613,6 +671,8 @@ def main():
     if args.gap_open is not None:
         return affine_main(args, b, A, B, S, Xs, ctx, ws, out, stream, timed, rank, world, local,
                            packed)
+    if args.traceback:
+        return traceback_main(args, b, ctx, stream, rank, world, local, packed)
 
     # persistent form, with per-level events kept for every timed step
     ctx.set_option(logan.OPT_TIMING, 1)
