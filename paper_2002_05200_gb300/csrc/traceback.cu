@@ -63,7 +63,14 @@ __device__ __forceinline__ TbRed tb_reduce(TbRed v, TbRed* sh) {
 struct TbItem {  // pass 1 output per item
     int32_t best, bi, bj, status;
     uint64_t words;  // predecessor-code words of anti-diagonals 1..d*
+    int32_t wide;    // the band outgrew the shared-memory ring: device-memory ring
+    int32_t pad;
 };
+
+// anti-diagonals held in shared memory up to this width (3 x 2048 int32 =
+// 24 KB per block); wider bands sweep again in the device-memory ring
+constexpr int kSmemCap = 2048;
+constexpr int TB_WIDE = 1;  // pass-1 status: retry in the device-memory ring
 
 struct TbArgs {
     KernelArgs ka;      // pools, items, scoring, ring
@@ -78,15 +85,15 @@ struct TbArgs {
 
 // The sweep of one item; RECORD: up to d* with the codes written.
 template <bool RECORD>
-__device__ void tb_sweep(const TbArgs& t, uint32_t id, int32_t* R, TbRed* sh) {
+__device__ void tb_sweep(const TbArgs& t, uint32_t id, int32_t* R, int cap, TbRed* sh) {
     const KernelArgs& ka = t.ka;
     const Item it = ka.items[id];
     const int dir = (it.flags & ITEM_LEFT) ? -1 : 1;
     const int m = int(it.m), n = int(it.n), X = it.X;
-    const int mask = int(ka.ring_cap) - 1;
+    const int mask = cap - 1;
     int32_t* A0 = R;
-    int32_t* A1 = R + ka.ring_cap;
-    int32_t* A2 = R + 2 * ka.ring_cap;
+    int32_t* A1 = R + cap;
+    int32_t* A2 = R + 2 * cap;
     const int dstar = RECORD ? t.info[id].bi + t.info[id].bj : INT_MAX;
     if (threadIdx.x == 0) A1[0] = 0;
     __syncthreads();
@@ -99,8 +106,8 @@ __device__ void tb_sweep(const TbArgs& t, uint32_t id, int32_t* R, TbRed* sh) {
         const int rlo = max(lo1, d - n), rhi = min(hi1 + 1, m);
         if (rlo > rhi) break;
         const int width = rhi - rlo + 1;
-        if (width > int(ka.ring_cap)) {
-            status = LOGAN_ERANGE;
+        if (width > cap) {
+            status = cap < int(ka.ring_cap) ? TB_WIDE : LOGAN_ERANGE;
             break;
         }
         if (RECORD && threadIdx.x == 0) {
@@ -173,6 +180,8 @@ __device__ void tb_sweep(const TbArgs& t, uint32_t id, int32_t* R, TbRed* sh) {
         r.bj = status ? 0 : bj;
         r.status = status;
         r.words = status ? 0 : words_best;
+        r.wide = cap > kSmemCap ? 1 : 0;
+        r.pad = 0;
         t.info[id] = r;
     }
 }
@@ -180,15 +189,28 @@ __device__ void tb_sweep(const TbArgs& t, uint32_t id, int32_t* R, TbRed* sh) {
 template <bool RECORD>
 __global__ void __launch_bounds__(kTbThreads) k_tb_sweep(TbArgs t) {
     __shared__ TbRed sh[kTbWarps];
+    __shared__ int32_t sring[3 * kSmemCap];
+    __shared__ int s_wide;
     int32_t* R = t.ka.ring + size_t(blockIdx.x) * 3u * t.ka.ring_cap;
+    const int gcap = int(t.ka.ring_cap);
     for (uint32_t id = blockIdx.x; id < t.ka.n_items; id += gridDim.x) {
         const Item it = t.ka.items[id];
         if (it.flags & ITEM_SKIP) {
-            if (!RECORD && threadIdx.x == 0) t.info[id] = TbItem{0, 0, 0, 0, 0ull};
+            if (!RECORD && threadIdx.x == 0) t.info[id] = TbItem{0, 0, 0, 0, 0ull, 0, 0};
             continue;
         }
-        if (RECORD && (t.info[id].status || t.info[id].bi + t.info[id].bj == 0)) continue;
-        tb_sweep<RECORD>(t, id, R, sh);
+        if (RECORD) {
+            if (t.info[id].status || t.info[id].bi + t.info[id].bj == 0) continue;
+            if (t.info[id].wide) tb_sweep<true>(t, id, R, gcap, sh);
+            else tb_sweep<true>(t, id, sring, kSmemCap, sh);
+        } else {
+            const bool fits = gcap > kSmemCap;
+            if (fits) tb_sweep<false>(t, id, sring, kSmemCap, sh);
+            __syncthreads();
+            if (threadIdx.x == 0) s_wide = !fits || t.info[id].status == TB_WIDE;
+            __syncthreads();
+            if (s_wide) tb_sweep<false>(t, id, R, gcap, sh);
+        }
         __syncthreads();
     }
 }
@@ -331,7 +353,8 @@ int run_traceback(int num_sms, const PoolDev& pa, const PoolDev& pb, bool same_p
     ExtRes* ext = S.get<ExtRes>(n_items);
     int32_t* mig = S.get<int32_t>(n_items);
     TbItem* tinfo = S.get<TbItem>(n_items);
-    const int grid = int(std::min<uint32_t>(n_items, uint32_t(num_sms) * 4u));
+    // 8 blocks of 256 threads fill an SM (24 KB of shared ring each)
+    const int grid = int(std::min<uint32_t>(n_items, uint32_t(num_sms) * 8u));
     const uint32_t cap = 1u << ring_log2;
     int32_t* ring = S.get<int32_t>(size_t(grid) * 3u * cap);
     if (!S.ok) return LOGAN_ENOMEM;

@@ -370,6 +370,18 @@ class Context:
                 X_per_pair.data_ptr() if X_per_pair is not None else None,
                 buf.data_ptr() if buf is not None else None, cap, start.data_ptr(),
                 count.data_ptr(), ctypes.byref(need), ctypes.c_void_p(stream.cuda_stream))
+        # a pair's codes never outnumber its two sequences' bases (+1): with
+        # that bound one call suffices; past 1 GiB of codes, ask for the
+        # exact size first (a second sweep of the batch)
+        sd = seeds.cpu().numpy().view(np.uint32).reshape(-1, 5) if n else np.zeros((0, 5), np.uint32)
+        la = A.lengths.cpu().numpy().view(np.uint32)
+        lb = B.lengths.cpu().numpy().view(np.uint32)
+        ok = (sd[:, 0] < la.size) & (sd[:, 1] < lb.size)
+        bound = int(la[sd[ok, 0]].astype(np.int64).sum() + lb[sd[ok, 1]].astype(np.int64).sum()) + n
+        if bound <= (1 << 28):
+            codes = torch.empty(max(bound, 1), dtype=torch.int32, device=dev)
+            _check(call(codes, bound), "logan_traceback_batch")
+            return codes[:max(need.value, 1)], start[:n], count[:n]
         rc = call(None, 0)
         if rc not in (OK, ENOMEM) or (rc == ENOMEM and need.value == 0):
             _check(rc, "logan_traceback_batch")
