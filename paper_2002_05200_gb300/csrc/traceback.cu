@@ -342,7 +342,7 @@ bool tb_scan(TbScratch& sc, uint64_t* v, uint64_t n, uint64_t* out, uint64_t* to
 
 namespace {
 
-int run_traceback(int num_sms, const PoolDev& pa, const PoolDev& pb, bool same_pool,
+int run_traceback(int num_sms, const PoolDev& pa, const PoolDev& pb,
                   const logan_seed_t* seeds, uint32_t n_pairs, Scoring sc, int32_t X,
                   const int32_t* Xs, uint32_t ring_log2, uint32_t* ops, uint64_t capacity,
                   uint64_t* op_start, uint32_t* op_count, uint64_t* needed, cudaStream_t s) {
@@ -370,7 +370,6 @@ int run_traceback(int num_sms, const PoolDev& pa, const PoolDev& pb, bool same_p
     t.ka.n_items = n_items;
     t.ka.sc = sc;
     t.info = tinfo;
-    (void)same_pool;
     k_tb_sweep<false><<<grid, kTbThreads, 0, s>>>(t);
     uint64_t* iw = S.get<uint64_t>(n_items + 1);
     uint64_t* ia = S.get<uint64_t>(n_items + 1);
@@ -463,7 +462,7 @@ extern "C" int logan_traceback_batch(logan_ctx_t* ctx, const logan_seqs_t* A,
             rc = S.ok ? LOGAN_ECUDA : LOGAN_ENOMEM;
         } else {
             if (same) pb = pa;
-            rc = run_traceback(sms, pa, pb, same, seeds, n_pairs, Scoring{match, mismatch, gap}, X,
+            rc = run_traceback(sms, pa, pb, seeds, n_pairs, Scoring{match, mismatch, gap}, X,
                                X_per_pair, uint32_t(ring_log2), ops, ops_capacity, op_start,
                                op_count, ops_needed, s);
         }

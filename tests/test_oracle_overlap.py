@@ -9,8 +9,6 @@ import pytest
 
 from oracle import overlap_oracle as ov
 
-COMP = {ord("A"): "T", ord("C"): "G", ord("G"): "C", ord("T"): "A"}
-
 
 def rand_reads(rng, n, lo, hi, genome=None):
     out = []
