@@ -354,6 +354,8 @@ def traceback_main(args, b, ctx, stream, rank, world, local, packed):
         with torch.cuda.stream(stream):
             ctx.traceback(A, B, S, sub.match, sub.mismatch, sub.gap, sub.X, Xs, stream=stream)
     torch.cuda.synchronize()
+    ctx.set_option(logan.OPT_TIMING, 1)
+    passes = []
     with ClockSampler(local) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -361,8 +363,10 @@ def traceback_main(args, b, ctx, stream, rank, world, local, packed):
             with torch.cuda.stream(stream):
                 codes, start, count = ctx.traceback(A, B, S, sub.match, sub.mismatch, sub.gap,
                                                     sub.X, Xs, stream=stream)
+            passes.append(ctx.traceback_stats())  # the call has synchronised
         e1.record(stream)
         e1.synchronize()
+    ctx.set_option(logan.OPT_TIMING, 0)
     ms = e0.elapsed_time(e1) / args.steps
     c = codes.cpu().numpy().view(np.uint32)
     st, ct = start.cpu().numpy(), count.cpu().numpy()
@@ -377,18 +381,60 @@ def traceback_main(args, b, ctx, stream, rank, world, local, packed):
         dj = int(n[op != 1].sum())
         span_ok &= (di, dj) == (int(r["endA"][p] - r["begA"][p]), int(r["endB"][p] - r["begB"][p]))
     cells = int(r["cells"][r["status"] == 0].sum())
+    mean = {k: float(np.mean([x[k] for x in passes])) for k in
+            ("sweep_ms", "record_ms", "walk_ms", "total_ms")}
+    # the dominant step is the recording sweep up to each best anti-diagonal:
+    # its algorithmic work is the recurrence's OPS_PER_CELL per evaluated cell
+    rec_cells = int(passes[-1]["record_cells"])
+    peak = logan.intpeak(local, 1, 2000)[0] / 1e9
+    achieved = OPS_PER_CELL * rec_cells / (mean["record_ms"] * 1e-3) / 1e9
     line = {"metric": METRIC + " -- alignment paths (logan_traceback_batch)",
             "value": sub.n_pairs / (ms * 1e-3), "unit": "paths/s", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "int32",
             "data": "synthetic",
             "config": dict(workload_config(b, args.workload, args.pairs), traced_pairs=sub.n_pairs),
-            "clocks": clk.summary(), "extension_cells": cells,
-            "gcups_equiv": cells / (ms * 1e-3) / 1e9,
+            "clocks": clk.summary(), "gpu_launches": int(passes[-1]["launches"]) * args.steps,
+            "extension_cells": cells, "gcups_equiv": cells / (ms * 1e-3) / 1e9,
+            "steps_ms": {"extension": round(mean["sweep_ms"], 3),
+                         "record": round(mean["record_ms"], 3),
+                         "walk": round(mean["walk_ms"], 3), "total": round(mean["total_ms"], 3)},
+            "record_cells": rec_cells,
+            "code_words": int(passes[-1]["code_words"]),
             "codes": int(ct.sum()), "paths_span_alignments": bool(span_ok),
-            "roofline": None,
-            "roofline_note": "two block-per-extension sweeps in device memory (the fallback "
-                             "kernel's layout) plus a walk per pair"}
+            "roofline": {
+                "bound": "alu",
+                "kernel": "recording sweep (k_tb_record_warp + k_tb_record_block retries)",
+                "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
+                "traffic": None, "ops_per_cell": OPS_PER_CELL, "cells": rec_cells,
+                "launch_ms": mean["record_ms"],
+                "peak_basis": "measured: int32 max chains on all SMs (logan_intpeak op 1); "
+                              "of measured"}}
+    if rank == 0 and not args.no_cpu_baseline:
+        # the traceback oracle, one pair per task on all host cores (ctypes
+        # releases the interpreter lock during each call)
+        from concurrent.futures import ThreadPoolExecutor
+
+        import oracle
+        threads = os.cpu_count() or 1
+
+        def one(p):
+            sd = sub.seeds[p]
+            X = int(sub.Xs[p]) if sub.Xs is not None else sub.X
+            oracle.pair_traceback(sub.seqA(p), sub.seqB(p), int(sd["posA"]), int(sd["posB"]),
+                                  int(sd["len"]), sub.match, sub.mismatch, sub.gap, X)
+
+        done, t0 = 0, time.perf_counter()
+        with ThreadPoolExecutor(threads) as ex:
+            while done < sub.n_pairs and time.perf_counter() - t0 < args.cpu_seconds:
+                chunk = list(range(done, min(done + threads, sub.n_pairs)))
+                list(ex.map(one, chunk))
+                done += len(chunk)
+        dt = time.perf_counter() - t0
+        line["cpu_baseline"] = {"value": done / dt, "unit": "paths/s", "cores": threads,
+                                "kind": "oracle",
+                                "sample": f"first {done} of the {sub.n_pairs} traced pairs "
+                                          f"({dt:.1f} s), traceback oracle, one pair per task"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 

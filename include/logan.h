@@ -278,17 +278,42 @@ int logan_overlap_keep(logan_ctx_t *ctx, const logan_result_t *results,
  *   whose band outgrows the fallback ring).  *ops_needed (host) receives the
  *   codes the batch needs; with ops_capacity below it the call returns
  *   LOGAN_ENOMEM after sizing (call again with more).
- * Work: each extension is swept twice by a block in device memory (once to
- * its end, once up to its best anti-diagonal recording 2-bit predecessor
- * codes) -- meant for the pairs a caller keeps, not whole raw batches.
+ * Work: the batch pipeline of logan_extend_batch finds every extension's
+ * best cell; then each extension is swept again up to its best
+ * anti-diagonal by a warp, recording 2-bit predecessor codes (a band wider
+ * than 512 rows is swept by a block of 256 threads instead: in shared
+ * memory up to 2048 rows, else in a device-memory ring); one thread per
+ * extension walks back.  The codes take about cells / 16 words of device
+ * memory -- meant for the pairs a caller keeps, not whole raw batches.
  * Temporary memory comes from the stream-ordered pool (cudaMallocAsync); the
- * call synchronises `stream`. */
+ * call synchronises `stream`.  With LOGAN_OPT_TIMING on, the call records
+ * CUDA events around its passes (logan_traceback_last_stats). */
 int logan_traceback_batch(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                           const logan_seqs_t *seqsB, const logan_seed_t *seeds,
                           uint32_t n_pairs, int32_t match, int32_t mismatch, int32_t gap,
                           int32_t X, const int32_t *X_per_pair, uint32_t *ops,
                           uint64_t ops_capacity, uint64_t *op_start, uint32_t *op_count,
                           uint64_t *ops_needed, void *stream);
+
+/* Device times of the last logan_traceback_batch call made on `ctx` with
+ * LOGAN_OPT_TIMING on (LOGAN_EINVAL if there was none):
+ *   sweep_ms     step 1: the batch pipeline (as logan_extend_batch) that
+ *                finds every extension's best cell;
+ *   record_ms    the sweeps up to each best anti-diagonal that write the
+ *                predecessor codes (warp form, then the block form for the
+ *                bands that outgrew a warp's ring);
+ *   walk_ms      the walks back from the best cells (run-length codes);
+ *   total_ms     the call's device work from its first launch to its last;
+ *   code_words   32-bit words of storage for predecessor codes;
+ *   record_cells cells the recording sweeps evaluated (a retried band's
+ *                final sweep only);
+ *   launches     kernels of this library the call launched. */
+typedef struct {
+    float sweep_ms, record_ms, walk_ms, total_ms;
+    uint64_t code_words, record_cells;
+    uint32_t launches;
+} logan_traceback_stats_t;
+int logan_traceback_last_stats(logan_ctx_t *ctx, logan_traceback_stats_t *stats);
 
 /*
  * Same operation and results as logan_extend_batch, for callers that cannot

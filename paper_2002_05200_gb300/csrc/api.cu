@@ -11,6 +11,7 @@
 #include <string>
 #include <vector>
 
+#include "ctx_ext.h"
 #include "internal.h"
 #include "../../include/logan.h"
 
@@ -89,7 +90,10 @@ struct logan_ctx {
     // graph cache
     std::vector<GraphEntry> graphs;
     uint64_t use_clock = 0;
+    // the last timed alignment-path call
+    TracebackTiming tb_timing;
 };
+
 
 namespace {
 
@@ -145,6 +149,27 @@ Layout make_layout(const logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t
     L.total = off;
     return L;
 }
+
+}  // namespace
+
+TracebackTiming* logan::ctx_traceback_timing(logan_ctx_t* c) { return &c->tb_timing; }
+
+void logan::extension_views(const logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
+                            uint32_t n_pairs, const void* ws, ExtensionViews* v) {
+    const Layout L = make_layout(c, A, B, n_pairs);
+    const char* w = static_cast<const char*>(ws);
+    v->wa = A->packed2bit ? static_cast<const uint32_t*>(A->bases)
+                          : reinterpret_cast<const uint32_t*>(w + L.wordsA);
+    v->wb = L.same ? v->wa
+                   : B->packed2bit ? static_cast<const uint32_t*>(B->bases)
+                                   : reinterpret_cast<const uint32_t*>(w + L.wordsB);
+    v->items = reinterpret_cast<const Item*>(w + L.items);
+    v->ext = reinterpret_cast<const ExtRes*>(w + L.ext);
+    v->info = reinterpret_cast<const PairInfo*>(w + L.info);
+    v->launches = c->launches_last;
+}
+
+namespace {
 
 bool params_ok(int32_t match, int32_t mismatch, int32_t gap, int32_t X) {
     auto a = [](int32_t v) { return v < 0 ? -int64_t(v) : int64_t(v); };

@@ -33,7 +33,7 @@ EXPORTED = ["logan_version", "logan_strerror", "logan_ctx_create", "logan_ctx_de
             "logan_workspace_size", "logan_extend_batch", "logan_extend_batch_plain",
             "logan_extend_batch_affine", "logan_overlap_candidates", "logan_overlap_pool_words",
             "logan_overlap_pool", "logan_overlap_seeds", "logan_overlap_keep",
-            "logan_traceback_batch",
+            "logan_traceback_batch", "logan_traceback_last_stats",
             "logan_set_option", "logan_get_option", "logan_num_levels", "logan_level_info",
             "logan_last_stats", "logan_call_stats", "logan_set_level_table",
             "logan_get_level_table", "logan_intpeak", "logan_autotune", "logan_autotune_save",
@@ -56,6 +56,13 @@ class StatsT(ctypes.Structure):
     _fields_ = [("level_ms", ctypes.c_float * (MAX_LEVELS + 1)), ("total_ms", ctypes.c_float),
                 ("items", ctypes.c_uint32 * (MAX_LEVELS + 1)),
                 ("cells", ctypes.c_uint64 * (MAX_LEVELS + 1)), ("launches", ctypes.c_uint32)]
+
+
+class TracebackStatsT(ctypes.Structure):
+    _fields_ = [("sweep_ms", ctypes.c_float), ("record_ms", ctypes.c_float),
+                ("walk_ms", ctypes.c_float), ("total_ms", ctypes.c_float),
+                ("code_words", ctypes.c_uint64), ("record_cells", ctypes.c_uint64),
+                ("launches", ctypes.c_uint32)]
 
 
 class RequestT(ctypes.Structure):
@@ -116,6 +123,7 @@ def lib():
         L.logan_traceback_batch.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT), p, u32,
                                             i32, i32, i32, i32, p, p, u64, p, p,
                                             ctypes.POINTER(u64), p]
+        L.logan_traceback_last_stats.argtypes = [p, ctypes.POINTER(TracebackStatsT)]
         L.logan_set_option.argtypes = [p, ctypes.c_int, i64]
         L.logan_get_option.argtypes = [p, ctypes.c_int, ctypes.POINTER(i64)]
         L.logan_level_info.argtypes = [ctypes.c_int, ctypes.POINTER(ctypes.c_int),
@@ -389,6 +397,16 @@ class Context:
         if need.value:
             _check(call(codes, need.value), "logan_traceback_batch")
         return codes, start[:n], count[:n]
+
+    def traceback_stats(self) -> dict:
+        """Device ms of the passes of the last traceback call made with
+        OPT_TIMING (logan_traceback_last_stats)."""
+        st = TracebackStatsT()
+        _check(lib().logan_traceback_last_stats(self._h, ctypes.byref(st)),
+               "logan_traceback_last_stats")
+        return dict(sweep_ms=st.sweep_ms, record_ms=st.record_ms, walk_ms=st.walk_ms,
+                    total_ms=st.total_ms, code_words=st.code_words,
+                    record_cells=st.record_cells, launches=st.launches)
 
     # ---- many-to-many overlap seeding (logan_overlap_*) ----
 

@@ -107,3 +107,33 @@ def test_invalid_pairs_have_no_path(ctx):
     bad = res["status"] != 0
     assert bad.any() and all(paths[p] == [] for p in np.flatnonzero(bad))
     check(b, paths, res)
+
+
+@pytest.mark.parametrize("median,X,n", [(3000, 300, 12), (10_000, 1500, 4)])
+def test_wide_bands_block_and_device_rings(ctx, median, X, n):
+    # unrelated pairs: bands past a warp's 512-row ring (the block form),
+    # and at X = 1500 on 10 kbp pairs past 2048 rows (the device-memory ring)
+    b = synth.lognormal_batch(n_pairs=n, median=median, lo=median - 500, hi=median + 500,
+                              related_frac=0.0, X=X, seed=5)
+    check(b, *gpu_paths(ctx, b, packed2bit=True))
+
+
+def test_timing_stats(ctx):
+    b = synth.uniform_pairs(n_pairs=50)
+    A, B, S, Xs = logan.batch_to_device(b)
+    ctx.set_option(logan.OPT_TIMING, 1)
+    try:
+        ctx.traceback(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs)
+        st = ctx.traceback_stats()
+        ext_launches = ctx.last_stats()["launches"]  # the call's own batch pipeline
+    finally:
+        ctx.set_option(logan.OPT_TIMING, 0)
+    assert st["sweep_ms"] > 0 and st["record_ms"] > 0 and st["walk_ms"] > 0
+    assert st["total_ms"] >= st["sweep_ms"] + st["record_ms"] + st["walk_ms"] - 1e-3
+    assert st["code_words"] > 0
+    # the recorded cells: every anti-diagonal up to the best one of each side
+    res = logan.results_to_numpy(ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs))
+    assert 0 < st["record_cells"] <= int(res["cells"].sum())
+    assert st["code_words"] >= st["record_cells"] // 16
+    # the pipeline's launches + prepare, two recording sweeps, walk, join
+    assert st["launches"] == ext_launches + 5
