@@ -570,6 +570,7 @@ def overlap_pipeline_main(args, rank, world, local):
     for _ in range(args.warmup):
         step()
     torch.cuda.synchronize()
+    ctx.set_option(logan.OPT_TIMING, 1)  # per-level events of the extension step
     with ClockSampler(local) as clk:
         e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
         e0.record(stream)
@@ -578,6 +579,8 @@ def overlap_pipeline_main(args, rank, world, local):
         e1.record(stream)
         e1.synchronize()
     ms = e0.elapsed_time(e1) / args.steps
+    lv = ctx.last_stats()
+    ctx.set_option(logan.OPT_TIMING, 0)
     # the candidate step alone
     f0, f1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     f0.record(stream)
@@ -620,9 +623,48 @@ def overlap_pipeline_main(args, rank, world, local):
             "seeding_ms": ms_front, "pairs_per_s": c.shape[0] / (ms * 1e-3),
             "true_overlaps_2kbp": n_true, "kept_true": kept_true,
             "recall_2kbp": kept_true / max(n_true, 1),
-            "precision": kept_true / max(int(keep.sum()), 1),
-            "roofline": None,
-            "roofline_note": "the extension kernels are profiled on the batch lines; the seeding step is sort-bound"}
+            "precision": kept_true / max(int(keep.sum()), 1)}
+    # roofline of the dominant step, the extension: its window levels run
+    # concurrently here (no single level dominates), so the whole step's
+    # cells over its device time
+    peak = logan.intpeak(local, 1, 2000)[0] / 1e9
+    ext_cells = cells  # the results' cells: a restarted band's repeats are not counted
+    achieved = OPS_PER_CELL * ext_cells / (lv["total_ms"] * 1e-3) / 1e9
+    line["roofline"] = {
+        "bound": "alu", "kernel": "extension step (all window levels)", "achieved": achieved,
+        "peak": peak, "unit": "Gop/s", "frac": achieved / peak, "traffic": None,
+        "ops_per_cell": OPS_PER_CELL, "cells": ext_cells, "launch_ms": float(lv["total_ms"]),
+        "peak_basis": "measured: int32 max chains on all SMs (logan_intpeak op 1); of measured"}
+    line["levels"] = {"ms": [round(float(x), 3) for x in lv["level_ms"]],
+                      "cells": [int(x) for x in lv["cells"]]}
+    if rank == 0 and not args.no_cpu_baseline:
+        # the oracle pipeline (numpy seeding, C extension on all host cores,
+        # threshold) on the reads that start in the genome's leftmost stretch:
+        # a bounded sample at the workload's coverage
+        import oracle
+        from oracle import overlap_oracle as ov
+        sel = np.argsort(rs, kind="stable")[:300]
+        reads_s = [b._seq(b.poolA, b.offA, b.lenA, 2 * int(r)) for r in sel]
+        t0 = time.perf_counter()
+        cs = ov.candidates(reads_s, k, fmin, fmax, mshared)
+        sd_s = ov.seeds(cs, [len(x) for x in reads_s], k)
+        both = reads_s + [ov.revcomp(x) for x in reads_s]
+        lA = np.array([len(x) for x in reads_s], np.uint32)
+        lB = np.array([len(x) for x in both], np.uint32)
+        oA = np.concatenate([[0], np.cumsum(lA.astype(np.uint64))[:-1]]).astype(np.uint64)
+        oB = np.concatenate([[0], np.cumsum(lB.astype(np.uint64))[:-1]]).astype(np.uint64)
+        pA = np.frombuffer(b"".join(reads_s), np.uint8)
+        pB = np.frombuffer(b"".join(both), np.uint8)
+        rres, used = oracle.batch(pA, oA, lA, pB, oB, lB, sd_s, 1, -1, -1, X)
+        ov.keep(rres["score"], lA[sd_s["idxA"]], lB[sd_s["idxB"]], sd_s["posA"], sd_s["posB"],
+                k, ratio_num, den, delta)
+        dt = time.perf_counter() - t0
+        ccells = int(rres["cells"][rres["status"] == 0].sum())
+        line["cpu_baseline"] = {
+            "value": ccells / dt / 1e9, "unit": "GCUPS", "cores": used, "kind": "oracle",
+            "sample": f"the 300 leftmost reads of the genome ({cs.size} candidates, {ccells} "
+                      f"cells, {dt:.1f} s): numpy seeding, C extension on all host cores, "
+                      "threshold"}
     if rank == 0:
         print(json.dumps(line), flush=True)
 
