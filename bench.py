@@ -146,6 +146,15 @@ def workload_config(b, name, pairs):
             "l2": f"inputs larger than L2 (packed pools {packed_mb:.0f} MB), no flush", **common}
 
 
+def measured_hbm_gbs():
+    """The machine's measured HBM copy bandwidth, when the peaks file is present."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return float(json.load(fh)["hbm_gbs"])
+    except (OSError, ValueError, KeyError):
+        return None
+
+
 def profiled_traffic(level: int, items: int):
     """DRAM bytes of one launch of `level` with `items` extensions, from the
     committed capture, or None when the kernel changed since."""
@@ -813,6 +822,15 @@ def main():
                       "rate; of measured",
         "nominal_peak": nominal,
         "nominal_basis": f"{n_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz"}
+    traffic = line["roofline"]["traffic"]
+    if traffic is not None and level_ms[dom] > 0:
+        # the secondary bound: DRAM bandwidth the launch used
+        hbm_peak = measured_hbm_gbs()
+        gbs = traffic / (level_ms[dom] * 1e-3) / 1e9
+        line["roofline"]["hbm"] = {"achieved_gbs": gbs, "peak_gbs": hbm_peak,
+                                   "frac": gbs / hbm_peak if hbm_peak else None,
+                                   "peak_basis": "measured copy bandwidth (MEASURED_PEAKS.json)"
+                                   if hbm_peak else None}
     if args.kernel_only:
         if rank == 0:
             print(json.dumps(line), flush=True)

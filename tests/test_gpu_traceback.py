@@ -137,3 +137,29 @@ def test_timing_stats(ctx):
     assert st["code_words"] >= st["record_cells"] // 16
     # the pipeline's launches + prepare, two recording sweeps, walk, join
     assert st["launches"] == ext_launches + 5
+
+
+@pytest.mark.parametrize("opt,val", [("OPT_GRAPHS", 1), ("OPT_CONCURRENT", 0),
+                                     ("OPT_MIGRATION_MB", 0), ("OPT_FORCE_LEVEL", 0)])
+def test_pipeline_options(ctx, opt, val):
+    # the call's first step is the batch pipeline: its options change the
+    # schedule, never the paths
+    import torch
+    b = synth.lognormal_batch(n_pairs=60, median=4000, lo=2000, hi=8000, seed=11)
+    key = getattr(logan, opt)
+    old = ctx.get_option(key)
+    ctx.set_option(key, val)
+    try:
+        stream = torch.cuda.Stream()  # graphs are captured on a non-default stream
+        with torch.cuda.stream(stream):
+            A, B, S, Xs = logan.batch_to_device(b, packed2bit=True)
+            codes, start, count = ctx.traceback(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs,
+                                                stream=stream)
+            res = ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, stream=stream)
+        stream.synchronize()
+    finally:
+        ctx.set_option(key, old)
+    c = codes.cpu().numpy().view(np.uint32)
+    st, ct = start.cpu().numpy(), count.cpu().numpy()
+    paths = [list(c[st[p]:st[p] + ct[p]]) for p in range(b.n_pairs)]
+    check(b, paths, logan.results_to_numpy(res))
