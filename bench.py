@@ -349,7 +349,7 @@ def run_reference(args, rank, world):
 # ---------------------------------------------------------------- GPU arm
 def traceback_main(args, b, ctx, stream, rank, world, local, packed):
     """Alignment paths of the first N pairs of the workload: time of
-    logan_traceback_batch (two sweeps per extension + the walks), paths
+    logan_traceback_batch (batch pipeline, recording sweep, walks), paths
     checked against the extension's coordinates; one JSON line."""
     import torch
 
