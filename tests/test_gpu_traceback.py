@@ -163,3 +163,23 @@ def test_pipeline_options(ctx, opt, val):
     st, ct = start.cpu().numpy(), count.cpu().numpy()
     paths = [list(c[st[p]:st[p] + ct[p]]) for p in range(b.n_pairs)]
     check(b, paths, logan.results_to_numpy(res))
+
+
+def test_bench_size_sampled(ctx):
+    """The benchmark's traced batch (the first 10,000 pairs of the
+    100,000-pair lognormal batch, 2-bit packed): every path spans its pair's
+    coordinates; a seeded sample of 24 pairs equals the oracle's paths and
+    rescores to the pair's score."""
+    b = synth.lognormal_batch().subset(np.arange(10_000))
+    paths, res = gpu_paths(ctx, b, packed2bit=True)
+    assert np.all(res["status"] == 0)
+    for p in range(b.n_pairs):
+        cc = np.asarray(paths[p], dtype=np.uint32)
+        n, op = cc >> 4, cc & 15
+        assert np.all(op <= 2) and np.all(n > 0)
+        assert int(n[op != 2].sum()) == int(res["endA"][p] - res["begA"][p]), p
+        assert int(n[op != 1].sum()) == int(res["endB"][p] - res["begB"][p]), p
+    idx = np.random.default_rng(77).choice(b.n_pairs, size=24, replace=False)
+    sub = b.subset(np.sort(idx))
+    sres = {f: res[f][np.sort(idx)] for f in ("status", "begA", "begB", "endA", "endB", "score")}
+    check(sub, [paths[p] for p in np.sort(idx)], sres)
