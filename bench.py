@@ -115,22 +115,34 @@ def workload(name: str, pairs: int, rank: int):
     return b
 
 
+# input pools smaller than this get an L2 flush (a 512 MB write) between
+# timed steps; larger ones exceed the 129 MB L2 several times over
+FLUSH_BELOW = 256 << 20
+
+
+def l2_note(b):
+    """How the timed steps keep L2 from serving the inputs (GPU arm)."""
+    packed = bool(b.meta.get("packed2bit", b.packed))
+    nbytes = b.pool_bases // (4 if packed else 1)
+    if nbytes < FLUSH_BELOW:
+        return (f"inputs smaller than L2 or near it ({nbytes / 1e6:.0f} MB): L2 flushed "
+                "(512 MB write) between timed steps, outside the step's events")
+    return f"inputs larger than L2 (pools {nbytes / 1e6:.0f} MB), no flush"
+
+
 def workload_config(b, name, pairs):
-    packed_mb = b.pool_bases / 4 / 1e6
     common = {"scoring": [1, -1, -1], "seed_len": 17,
               "parallelism": "replicas (independent pairs per GPU, no collective)"}
     if name == "uniform_pairs":
         return {"workload": name, "pairs": pairs, "length": 2000, "error_rate": 0.15,
                 "X": 50, "input": "uint8 ASCII (packed on the GPU)",
-                "l2": "inputs smaller than L2 (4 MB): L2 flushed (512 MB write) between timed "
-                      "steps, outside the step's events",
-                **common}
+                "l2": l2_note(b), **common}
     if name == "uneven_batch":
         return {"workload": name, "pairs": pairs,
                 "length_classes": "60/30/9/1 % in [1k,5k]/[5k,50k]/[50k,200k]/[200k,1M]",
                 "error_rate": "U[0.05, 0.20] per pair", "X": "per pair from {10,50,100,500}",
                 "input": "2-bit packed",
-                "l2": f"inputs larger than L2 (packed pools {packed_mb:.0f} MB), no flush", **common}
+                "l2": l2_note(b), **common}
     if name == "overlap_batch":
         return {"workload": name, "pairs": pairs, "genome_bp": b.meta["genome_len"],
                 "reads": b.meta["n_reads"], "read_len": "lognormal, mean 10 kbp, sigma 0.5",
@@ -138,12 +150,11 @@ def workload_config(b, name, pairs):
                 "errors": "12 % (6 % ins, 4 % del, 2 % sub)",
                 "true_overlaps": 0.3, "spurious": "0.7, one planted shared 17-mer (B copied)",
                 "X": 50, "input": "2-bit packed, one shared pool",
-                "l2": f"inputs larger than L2 (packed pool {packed_mb:.0f} MB), no flush",
-                **common}
+                "l2": l2_note(b), **common}
     return {"workload": name, "pairs": pairs, "median_len": 10_000,
             "len_sigma": 0.5, "len_clip": [1000, 30000], "related_frac": 0.8,
             "error_rate": 0.12, "X": 100, "input": "2-bit packed",
-            "l2": f"inputs larger than L2 (packed pools {packed_mb:.0f} MB), no flush", **common}
+            "l2": l2_note(b), **common}
 
 
 def measured_hbm_gbs():
@@ -731,7 +742,7 @@ def main():
 
     # inputs smaller than L2 (129 MB): flush L2 between timed steps by writing a
     # 512 MB buffer, outside each step's own pair of events
-    small = b.pool_bases // (4 if packed else 1) < (256 << 20)
+    small = b.pool_bases // (4 if packed else 1) < FLUSH_BELOW
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}") if small else None
 
     def timed(fn, steps, warmup):

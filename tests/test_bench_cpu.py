@@ -1,0 +1,44 @@
+"""bench.py's reference arm on the CPU (the oracle on a tiny batch): one JSON
+line with the contract's keys, the reference arm's own cpu_baseline and a
+zero-byte e2e; a second rank prints nothing."""
+import json
+import os
+import subprocess
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def run(args, env=None):
+    e = dict(os.environ)
+    e.update(env or {})
+    r = subprocess.run([sys.executable, os.path.join(ROOT, "bench.py"), *args], cwd=ROOT,
+                       capture_output=True, text=True, timeout=600, env=e)
+    assert r.returncode == 0, r.stderr[-2000:]
+    return [json.loads(x) for x in r.stdout.splitlines() if x.startswith("{")]
+
+
+@pytest.mark.parametrize("workload", ["lognormal_batch", "uniform_pairs"])
+def test_reference_line(workload):
+    lines = run(["--impl", "reference", "--workload", workload, "--pairs", "200",
+                 "--steps", "2", "--warmup", "1", "--cpu-seconds", "1"])
+    assert len(lines) == 1
+    j = lines[0]
+    for k in ("metric", "value", "unit", "n_gpus", "steps", "warmup", "ms_per_step",
+              "higher_is_better", "scaling", "vs_baseline", "dtype", "data", "config"):
+        assert k in j, k
+    assert j["impl"] == "reference" and j["unit"] == "GCUPS" and j["value"] > 0
+    assert j["steps"] == 2 and j["warmup"] == 1 and j["higher_is_better"] is True
+    assert j["config"]["workload"] == workload and "l2" in j["config"]
+    cb = j["cpu_baseline"]
+    assert cb["kind"] == "oracle" and cb["value"] == j["value"] and cb["cores"] >= 1
+    assert j["e2e"] == {"value": j["value"], "unit": "GCUPS", "h2d_bytes_per_step": 0,
+                        "d2h_bytes_per_step": 0}
+
+
+def test_reference_other_rank_is_silent():
+    lines = run(["--impl", "reference", "--pairs", "50", "--steps", "1", "--warmup", "0",
+                 "--cpu-seconds", "1"], env={"RANK": "1", "WORLD_SIZE": "2"})
+    assert lines == []
