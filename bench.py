@@ -745,20 +745,26 @@ def main():
     small = b.pool_bases // (4 if packed else 1) < FLUSH_BELOW
     flush_buf = torch.empty(512 << 20, dtype=torch.uint8, device=f"cuda:{local}") if small else None
 
+    step_stats = {}  # fn -> (median, best) ms of its timed steps
+
     def timed(fn, steps, warmup):
         with torch.cuda.stream(stream):
             for _ in range(warmup):
                 fn()
         barrier()
         if flush_buf is None:
-            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-            e0.record(stream)
-            for _ in range(steps):
+            # one event between consecutive steps: the total is the span of
+            # all K steps, and each step's own time gives median and best
+            evs = [torch.cuda.Event(enable_timing=True) for _ in range(steps + 1)]
+            evs[0].record(stream)
+            for k in range(steps):
                 fn()
-            e1.record(stream)
-            e1.synchronize()
+                evs[k + 1].record(stream)
+            evs[-1].synchronize()
             barrier()
-            ms = e0.elapsed_time(e1)
+            ms = evs[0].elapsed_time(evs[-1])
+            per = [evs[k].elapsed_time(evs[k + 1]) for k in range(steps)]
+            step_stats[fn] = (statistics.median(per), min(per))
         else:
             evs = []
             for _ in range(steps):
@@ -771,7 +777,9 @@ def main():
                 evs.append((a, z))
             torch.cuda.synchronize()
             barrier()
-            ms = sum(a.elapsed_time(z) for a, z in evs)
+            per = [a.elapsed_time(z) for a, z in evs]
+            ms = sum(per)
+            step_stats[fn] = (statistics.median(per), min(per))
         if world > 1:
             ms, _ = shard.reduce_step(ms, 0, device=f"cuda:{local}")
         return ms / steps
@@ -822,6 +830,11 @@ def main():
             "cells_per_step": tot_cells,
             "levels": {"ms": [round(float(v), 4) for v in level_ms],
                        "items": last["items"], "cells": last["cells"]}}
+    if step in step_stats:
+        med, best = step_stats[step]
+        line["step_ms"] = {"median": med, "best": best,
+                           "value_at_median": tot_cells / (med * 1e-3) / 1e9,
+                           "value_at_best": tot_cells / (best * 1e-3) / 1e9}
     line["roofline"] = {
         "bound": "alu", "kernel": f"window level {dom}" if dom < nl else "ring fallback",
         "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
