@@ -9,7 +9,9 @@ The oracle is checked against things other than itself:
   * hand-derived worked examples (tests/golden/worked_examples.txt);
   * invariants on random inputs (bounds, full-DP upper bound, symmetry);
   * the X-monotonicity counterexample of the chosen reading;
-  * input validation.
+  * input validation;
+and cross-checked (not pinned) against a second sweep kept as per-anti-
+diagonal dictionaries on every tiny input size.
 """
 import itertools
 import os
@@ -268,3 +270,55 @@ def test_batch_matches_single_pairs():
         r = oracle.pair(b.seqA(p), b.seqB(p), int(s["posA"]), int(s["posB"]), int(s["len"]),
                         b.match, b.mismatch, b.gap, int(b.Xs[p]))
         assert tuple(r) == tuple(res[p])
+
+
+def _sweep_dicts(a: bytes, b: bytes, M: int, MM: int, G: int, X: int):
+    """X-drop sweep kept as one dict {i: score} of live cells per
+    anti-diagonal (readings R1-R10), written apart from the C oracle's
+    arrays: a cross-check of its bookkeeping, not a pin."""
+    m, n = len(a), len(b)
+    live = {0: {0: 0}}     # d -> {i: score} of live cells
+    rng = {0: (0, 0)}      # d -> stored (trimmed) range
+    best, bi, bj, cells = 0, 0, 0, 0
+    for d in range(1, m + n + 1):
+        lo1, hi1 = rng[d - 1]
+        lo, hi = max(lo1, d - n), min(hi1 + 1, m)
+        if lo > hi:
+            break
+        cur = {}
+        for i in range(lo, hi + 1):
+            j = d - i
+            terms = []
+            if i > 0 and j > 0 and d >= 2 and (i - 1) in live[d - 2]:
+                terms.append(live[d - 2][i - 1] + (M if a[i - 1] == b[j - 1] else MM))
+            if i > 0 and (i - 1) in live[d - 1]:
+                terms.append(live[d - 1][i - 1] + G)
+            if j > 0 and i in live[d - 1]:
+                terms.append(live[d - 1][i] + G)
+            if terms and max(terms) >= best - X:
+                cur[i] = max(terms)
+        cells += hi - lo + 1
+        if not cur:
+            break
+        top = max(cur.values())
+        if top > best:
+            best = top
+            bi = min(i for i, v in cur.items() if v == top)
+            bj = d - bi
+        live[d] = cur
+        rng[d] = (min(cur), max(cur))
+    return best, bi, bj, cells
+
+
+@pytest.mark.parametrize("scheme", [(1, -1, -1), (2, -3, -2), (1, -1, 0)])
+def test_finite_x_matches_dict_sweep(scheme):
+    M, MM, G = scheme
+    rng = np.random.default_rng(31)
+    for _ in range(4000):
+        m, n = (int(v) for v in rng.integers(0, 13, size=2))
+        alpha = np.frombuffer(b"AC", np.uint8)
+        a = alpha[rng.integers(0, 2, m)].tobytes()
+        b = alpha[rng.integers(0, 2, n)].tobytes()
+        X = int(rng.integers(0, 9))
+        assert tuple(oracle.extend(a, b, M, MM, G, X)) == _sweep_dicts(a, b, M, MM, G, X), \
+            (a, b, X)
