@@ -166,3 +166,61 @@ def test_validation():
     assert not oracle.affine_params_valid(1, -1, -2, -1, -1)     # X < 0
     r = oracle.affine_pair(b"ACGN", b"ACGT", 0, 0, 0, 1, -1, -2, -1, 10)
     assert r["status"] == oracle.INVALID
+
+
+def _affine_sweep_dicts(a, b, M, MM, go, ge, X):
+    """The affine X-drop sweep with one dict {i: (H, E, F)} of live cells per
+    anti-diagonal (None = -infinity), written apart from the C oracle's
+    arrays and existence flags: a cross-check, not a pin."""
+    m, n = len(a), len(b)
+
+    def mx(*v):
+        v = [x for x in v if x is not None]
+        return max(v) if v else None
+
+    live = {0: {0: (0, None, None)}}
+    rng = {0: (0, 0)}
+    best, bi, bj, cells = 0, 0, 0, 0
+    for d in range(1, m + n + 1):
+        lo1, hi1 = rng[d - 1]
+        lo, hi = max(lo1, d - n), min(hi1 + 1, m)
+        if lo > hi:
+            break
+        cur = {}
+        for i in range(lo, hi + 1):
+            j = d - i
+            left = live[d - 1].get(i) if j > 0 else None     # (i, j-1)
+            up = live[d - 1].get(i - 1) if i > 0 else None   # (i-1, j)
+            diag = live[d - 2].get(i - 1) if (i > 0 and j > 0 and d >= 2) else None
+            E = mx(left[1] + ge if left and left[1] is not None else None,
+                   left[0] + go + ge if left else None)
+            F = mx(up[2] + ge if up and up[2] is not None else None,
+                   up[0] + go + ge if up else None)
+            H = mx(diag[0] + (M if a[i - 1] == b[j - 1] else MM) if diag else None, E, F)
+            if H is not None and H >= best - X:
+                cur[i] = (H, E, F)
+        cells += hi - lo + 1
+        if not cur:
+            break
+        top = max(v[0] for v in cur.values())
+        if top > best:
+            best = top
+            bi = min(i for i, v in cur.items() if v[0] == top)
+            bj = d - bi
+        live[d] = cur
+        rng[d] = (min(cur), max(cur))
+    return best, bi, bj, cells
+
+
+@pytest.mark.parametrize("M,MM,go,ge", [(1, -1, -2, -1), (2, -3, -3, -1), (1, -1, 0, -1),
+                                        (1, 0, -1, 0)])
+def test_finite_x_matches_dict_sweep(M, MM, go, ge):
+    rng = np.random.default_rng(41)
+    alpha = np.frombuffer(b"AC", np.uint8)
+    for _ in range(3000):
+        m, n = (int(v) for v in rng.integers(0, 12, size=2))
+        a = alpha[rng.integers(0, 2, m)].tobytes()
+        b = alpha[rng.integers(0, 2, n)].tobytes()
+        X = int(rng.integers(0, 9))
+        assert tuple(oracle.affine_extend(a, b, M, MM, go, ge, X)) == \
+            _affine_sweep_dicts(a, b, M, MM, go, ge, X), (a, b, X)
