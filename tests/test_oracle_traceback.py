@@ -106,3 +106,67 @@ def test_pair_paths_span_the_reported_coordinates():
         ops = oracle.pair_traceback(A, B, p, p, k, 1, -1, -1, X)
         s, di, dj = rescore(A[r["begA"]:], B[r["begB"]:], ops, 1, -1, -1)
         assert (s, di, dj) == (r["score"], r["endA"] - r["begA"], r["endB"] - r["begB"])
+
+
+def _path_dicts(a, b, match, mismatch, gap, X):
+    """The X-drop sweep with one dict {i: (score, how)} of live cells per
+    anti-diagonal (how: 'M' diagonal, 'I' vertical, 'D' horizontal, the
+    first in that order among the terms giving the score), and the walk
+    back from the best cell: a cross-check of the oracle's tie rule and
+    walk at finite X, not a pin."""
+    m, n = len(a), len(b)
+    live = {0: {0: (0, None)}}
+    rng = {0: (0, 0)}
+    best, bi, bj = 0, 0, 0
+    for d in range(1, m + n + 1):
+        lo1, hi1 = rng[d - 1]
+        lo, hi = max(lo1, d - n), min(hi1 + 1, m)
+        if lo > hi:
+            break
+        cur = {}
+        for i in range(lo, hi + 1):
+            j = d - i
+            terms = []
+            if i > 0 and j > 0 and d >= 2 and (i - 1) in live[d - 2]:
+                terms.append((live[d - 2][i - 1][0] + (match if a[i - 1] == b[j - 1] else mismatch),
+                              "M"))
+            if i > 0 and (i - 1) in live[d - 1]:
+                terms.append((live[d - 1][i - 1][0] + gap, "I"))
+            if j > 0 and i in live[d - 1]:
+                terms.append((live[d - 1][i][0] + gap, "D"))
+            if terms:
+                s = max(t[0] for t in terms)
+                if s >= best - X:
+                    cur[i] = (s, next(h for v, h in terms if v == s))
+        if not cur:
+            break
+        top = max(v[0] for v in cur.values())
+        if top > best:
+            best = top
+            bi = min(i for i, v in cur.items() if v[0] == top)
+            bj = d - bi
+        live[d] = cur
+        rng[d] = (min(cur), max(cur))
+    ops, i, j = [], bi, bj
+    while i + j:
+        h = live[i + j][i][1]
+        ops.append(h)
+        if h == "M":
+            i, j = i - 1, j - 1
+        elif h == "I":
+            i -= 1
+        else:
+            j -= 1
+    return best, bi, bj, "".join(reversed(ops))
+
+
+@pytest.mark.parametrize("scheme", [(1, -1, -1), (2, -3, -2), (1, -1, 0)])
+def test_finite_x_paths_match_dict_sweep(scheme):
+    match, mismatch, gap = scheme
+    rng = np.random.default_rng(51)
+    for _ in range(3000):
+        m, n = (int(v) for v in rng.integers(0, 13, size=2))
+        a, b = rand(rng, m, b"AC"), rand(rng, n, b"AC")
+        X = int(rng.integers(0, 9))
+        best, bi, bj, _, ops = oracle.traceback(a, b, match, mismatch, gap, X)
+        assert (best, bi, bj, ops) == _path_dicts(a, b, match, mismatch, gap, X), (a, b, X)
