@@ -39,16 +39,23 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "X-drop GCUPS (computed cells), batched vs plain launch; serving p50/p99 ms"
-# DRAM traffic of the level-2 kernel (k_group<8, 16>) from one ncu capture
-# (dram__bytes_read.sum + dram__bytes_write.sum of its launch on the
-# 24,000-pair lognormal batch, which starts 48,000 extensions there).  Scaled
-# to a launch by the extensions it starts; reported only while the kernel's
-# sources are the ones captured.
-PROFILED_TRAFFIC = {"level": 2, "bytes": 114.030336e6 + 7.497472e6, "items": 48_000,
-                    "sources": ("xdrop_group.cu", "logan_dev.cuh", "internal.h"),
-                    "sha1": "c11e7e7940fb707e8c6dc2852623834331fe3cd4"}
+# From one ncu capture of the level-2 kernel (k_group<8, 16>) on the
+# 24,000-pair lognormal batch (48,000 extensions started):
+#   bytes     dram__bytes_read.sum + dram__bytes_write.sum of the launch,
+#             scaled to a launch by the extensions it starts;
+#   fma_share the share of its executed warp instructions that issue to the
+#             FMA pipe (IMAD, from sass__inst_executed_per_opcode), the rest
+#             going to the ALU pipe or to pipes that are not near a limit.
+# Reported only while the kernel's sources are the ones captured.
+PROFILED = {"level": 2, "bytes": 114.030336e6 + 7.497472e6, "items": 48_000,
+            "fma_share": 126.0 / 347.0,
+            "sources": ("xdrop_group.cu", "logan_dev.cuh", "internal.h"),
+            "sha1": "c11e7e7940fb707e8c6dc2852623834331fe3cd4"}
 OPS_PER_CELL_AFFINE = 12  # Gotoh per cell: compare, diag add, E: 2 adds + max, F: 2 adds + max, 2 max, X-drop compare, select
-OPS_PER_CELL = 8          # Algorithm 2 per cell: compare, add, 2 gap adds, 2 max, X-drop compare, select
+# The scope table's count for the linear recurrence, per cell: substitution
+# select, diag + substitution, max(up, left), + gap and max with the diagonal
+# term, the X-drop compare and select, the running-max contribution
+OPS_PER_CELL = 7
 LANES_PER_SM = 128        # nominal: 4 sub-partitions x 32 lanes per clock (Blackwell SM)
 
 
@@ -166,20 +173,37 @@ def measured_hbm_gbs():
         return None
 
 
-def profiled_traffic(level: int, items: int):
-    """DRAM bytes of one launch of `level` with `items` extensions, from the
-    committed capture, or None when the kernel changed since."""
+def _profile_current(level: int) -> bool:
+    """True while `level` is the captured kernel and its sources are unchanged."""
     import hashlib
-    p = PROFILED_TRAFFIC
+    p = PROFILED
     if level != p["level"]:
-        return None
+        return False
     h = hashlib.sha1()
     for f in p["sources"]:
         with open(os.path.join(ROOT, "paper_2002_05200_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
-    if h.hexdigest() != p["sha1"]:
+    return h.hexdigest() == p["sha1"]
+
+
+def profiled_traffic(level: int, items: int):
+    """DRAM bytes of one launch of `level` with `items` extensions, from the
+    committed capture, or None when the kernel changed since."""
+    if not _profile_current(level):
         return None
-    return p["bytes"] * items / p["items"]
+    return PROFILED["bytes"] * items / PROFILED["items"]
+
+
+def mixed_ceiling(level: int, alu: float, fma: float, issue: float):
+    """Ceiling of the captured kernel's own instruction stream: a share f of
+    its warp instructions on the FMA pipe (measured rate `fma`), the rest on
+    the ALU pipe (rate `alu`), all through one issue port per sub-partition
+    (rate `issue`); the pipes run in parallel, so the stream's rate is
+    min(alu / (1 - f), fma / f, issue).  None when the capture is stale."""
+    if not _profile_current(level):
+        return None
+    f = PROFILED["fma_share"]
+    return min(alu / (1.0 - f), fma / f, issue)
 
 
 # ---------------------------------------------------------------- clocks
@@ -835,6 +859,9 @@ def main():
         line["step_ms"] = {"median": med, "best": best,
                            "value_at_median": tot_cells / (med * 1e-3) / 1e9,
                            "value_at_best": tot_cells / (best * 1e-3) / 1e9}
+    fma_rate = logan.intpeak(local, 8, 2000)[0] / 1e9     # int multiply-add (FMA pipe)
+    issue_rate = logan.intpeak(local, 9, 2000)[0] / 1e9   # fp32 add: one warp instr per issue slot
+    mixed = mixed_ceiling(dom, peak, fma_rate, issue_rate)
     line["roofline"] = {
         "bound": "alu", "kernel": f"window level {dom}" if dom < nl else "ring fallback",
         "achieved": achieved, "peak": peak, "unit": "Gop/s", "frac": achieved / peak,
@@ -844,7 +871,13 @@ def main():
         "ops_per_cell": OPS_PER_CELL, "cells": dom_cells, "launch_ms": float(level_ms[dom]),
         "peak_basis": "measured: int32 max chains on all SMs (logan_intpeak op 1), the ALU-pipe "
                       "rate; of measured",
-        "nominal_peak": nominal,
+        "peak_mixed": mixed, "frac_mixed": achieved / mixed if mixed else None,
+        "mixed_basis": "the kernel's measured instruction mix (FMA-pipe share "
+                       f"{PROFILED['fma_share']:.3f} from ncu) over the measured ALU "
+                       f"({peak:.0f}), FMA-pipe multiply-add ({fma_rate:.0f}) and issue "
+                       f"({issue_rate:.0f} Gop/s) rates: min(alu/(1-f), fma/f, issue); "
+                       "null once the kernel changed since the capture",
+        "nominal_peak": nominal, "frac_nominal": achieved / nominal,
         "nominal_basis": f"{n_sms} SMs x {LANES_PER_SM} lanes x {sm_max:.0f} MHz"}
     traffic = line["roofline"]["traffic"]
     if traffic is not None and level_ms[dom] > 0:

@@ -316,8 +316,9 @@ typedef struct {
 int logan_traceback_last_stats(logan_ctx_t *ctx, logan_traceback_stats_t *stats);
 
 /*
- * Same operation and results as logan_extend_batch, for callers that cannot
- * allocate device memory -- e.g. a host whose GPU memory is owned by another
+ * Same operation and results as logan_extend_batch (except for pairs whose
+ * band is wider than LOGAN_NOALLOC_RING_ROWS, see below), for callers that
+ * cannot allocate device memory -- e.g. a host whose GPU memory is owned by another
  * allocator, or a latency-critical loop that must not call cudaMalloc /
  * cudaFree (both can synchronise the device and stall unrelated streams).
  * The paper has no counterpart: this is a deployment variant of the batch
@@ -329,12 +330,17 @@ int logan_traceback_last_stats(logan_ctx_t *ctx, logan_traceback_stats_t *stats)
  *     band-state records are kept (LOGAN_OPT_MIGRATION_MB is 0 for the call)
  *     and all levels run on `stream` (LOGAN_OPT_CONCURRENT is 0).
  *   - The fallback window for very wide bands is LOGAN_NOALLOC_RING_ROWS
- *     rows (wider bands give LOGAN_ERANGE for that pair).
+ *     rows, where logan_extend_batch has 65,536 by default: a pair with a
+ *     band between those widths gets LOGAN_ERANGE here (every other pair
+ *     the same result as logan_extend_batch).
  *   - A batch whose scratch need (logan_workspace_size with that window)
  *     exceeds LOGAN_NOALLOC_SCRATCH_BYTES is rejected with LOGAN_ENOMEM
  *     before anything is launched (about 110K pairs of 2-bit input fit).
  *   - The first call on a device looks up the array's device address (with
- *     that device current); make that first call before any stream capture.
+ *     that device current) and keeps it for the life of the process; make
+ *     that first call before any stream capture, and do not use this call
+ *     after a cudaDeviceReset of that device (the kept address would be
+ *     stale).
  *   - All no-alloc calls on a device share the array, which keeps the last
  *     call's contents; the pipeline initialises everything it reads, so no
  *     clearing is needed between calls, but calls that overlap on the GPU

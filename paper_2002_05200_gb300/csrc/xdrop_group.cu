@@ -27,9 +27,12 @@
 // is paid once per warp.  Window slides, result writes and item refills run
 // once per three steps at the loop top (the window keeps three rows of slack
 // above the band), so the unrolled steps hold only the hot path.  A band that
-// outgrows the window is handed to the next, wider level, which recomputes
-// it.  Items with X > kGroupMaxX never start here (binning sends them to the
-// multi-warp levels): the keys need (X + max score) * W < 2^31.
+// outgrows the window writes its last two anti-diagonals and scalars to a
+// band-state record and is handed to the next, wider level, which resumes
+// from the record (unit_init); only when the record pool is full does that
+// level recompute the extension from the start.  Items with X > kGroupMaxX
+// never start here (binning sends them to the multi-warp levels): the keys
+// need (X + max score) * W < 2^31.
 #include "internal.h"
 
 namespace logan {
