@@ -89,15 +89,35 @@ def parse():
     ap.add_argument("--traceback", type=int, default=0,
                     help="time logan_traceback_batch on the first N pairs of the workload "
                          "instead (alignment paths)")
+    ap.add_argument("--shard", default="replicas", choices=["replicas", "lpt"],
+                    help="N > 1: replicas = every rank runs its own batch (weak scaling); "
+                         "lpt = the ranks split ONE batch by longest-processing-time over "
+                         "pair lengths and the results are gathered (strong scaling)")
+    ap.add_argument("--long-item", type=int, default=None,
+                    help="LOGAN_OPT_LONG_ITEM for the timed calls (default: the library's "
+                         "automatic rule)")
+    ap.add_argument("--packed16", type=int, default=None, choices=[0, 1],
+                    help="LOGAN_OPT_PACKED16 for the timed calls (default: the library's, 1)")
     ap.add_argument("--concurrent", type=int, default=1, choices=[0, 1],
                     help="1: the start levels of a batch run concurrently (default); "
                          "0: level after level on one stream")
     ap.add_argument("--serving-rate", type=float, default=80.0, help="requests per second")
-    ap.add_argument("--serving-requests", type=int, default=240)
+    ap.add_argument("--serving-requests", type=int, default=2000,
+                    help="sweep: measured requests per point (or --serving-seconds)")
+    ap.add_argument("--serving-seconds", type=float, default=60.0,
+                    help="sweep: measured seconds per point (or --serving-requests)")
+    ap.add_argument("--serving-warmup", type=float, default=5.0)
     ap.add_argument("--serving-budget-gb", type=float, default=16.0)
+    ap.add_argument("--serving-budgets", type=str, default="",
+                    help="sweep: comma-separated budgets in GB (default: --serving-budget-gb)")
     ap.add_argument("--serving-inflight", type=int, default=32)
+    ap.add_argument("--serving-library", type=int, default=30_000,
+                    help="sweep: pairs in the library the requests draw from")
+    ap.add_argument("--serving-line-library", type=int, default=8_000,
+                    help="pairs in the library of the headline line's short serving run")
     ap.add_argument("--serving-sweep", type=str, default="",
-                    help="comma-separated rates: print one serving JSON line per rate and exit")
+                    help="comma-separated rates: print one serving JSON line per rate "
+                         "(and budget) and exit")
     return ap.parse_args()
 
 
@@ -263,76 +283,178 @@ class ClockSampler:
 
 
 # ---------------------------------------------------------------- serving
-def serving_run(ctx, rate: float, n_requests: int, budget_gb: float, inflight: int,
-                distinct: int = 12, seed: int = 4):
-    """Poisson arrivals of requests (log-uniform 1..10,000 pairs, uneven
-    lengths 1 kbp-1 Mbp, X = 50) drawn from a pool of `distinct` pre-built
-    requests; latency = submit -> results in host memory."""
+def serving_library(pairs: int, seed: int = 5):
+    """The pair library the serving requests draw from (uneven lengths
+    1 kbp - 1 Mbp, error U[5, 20] %, X = 50), packed."""
+    from paper_2002_05200_gb300 import synth
+    return synth.serving_library(pairs, seed=seed, X=50)
+
+
+def library_results(ctx, lib):
+    """Every library pair extended once, alone in one batch: the reference
+    each served request's results must equal."""
     import torch
 
+    from paper_2002_05200_gb300 import logan
+    b = lib.request(np.arange(lib.n_pairs), "library")
+    A, B, S, Xs = logan.batch_to_device(b, packed2bit=True)
+    o = ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs)
+    torch.cuda.synchronize()
+    return logan.results_to_numpy(o)
+
+
+def serving_run(ctx, lib, lib_res, rate: float, budget_gb: float, inflight: int,
+                warmup_s: float = 5.0, min_s: float = 60.0, min_requests: int = 2000,
+                seed: int = 4):
+    """Poisson arrivals at `rate` req/s of fresh requests: each one draws
+    round(exp(U[0, ln 10^4])) pairs at random from the library, so no two
+    requests hold the same pairs in the same order.  Arrivals during the
+    first `warmup_s` seconds are served but not measured; measured arrivals
+    continue until `min_s` seconds have passed or `min_requests` measured
+    requests were submitted, whichever comes first.
+
+    Latency is taken on the host: submit -> the completion seen by a poller
+    thread (logan_server_poll every ~1 ms); the library's own
+    submit-to-results time is reported beside it.  Every request's results
+    must equal the library pairs' results extended alone."""
     from paper_2002_05200_gb300 import logan, synth
-    rng = np.random.default_rng(seed)
-    pool = [logan.HostRequest(b) for _, b in synth.serving_requests(distinct, rate, seed=seed)]
-    # reference results of each distinct request, run alone
-    alone = []
-    for h in pool:
-        A, B, S, Xs = logan.batch_to_device(h.batch, packed2bit=True)
-        o = ctx.extend(A, B, S, h.batch.match, h.batch.mismatch, h.batch.gap, h.batch.X, Xs)
-        torch.cuda.synchronize()
-        alone.append(logan.results_to_numpy(o))
-        del A, B, S, Xs, o
-    gaps = rng.exponential(1.0 / rate, size=n_requests)
-    arrivals = np.cumsum(gaps) - gaps[0]
-    which = rng.integers(0, distinct, size=n_requests)
-    bufs = [torch.empty((max(1, pool[w].n_pairs), 10), dtype=torch.int32).pin_memory()
-            for w in which]
+    rng = np.random.default_rng([seed, int(rate * 1000)])  # arrivals
     srv = logan.Server(ctx, budget_bytes=int(budget_gb * (1 << 30)), max_inflight=inflight)
-    lat = [None] * n_requests
-    done_at = [0.0] * n_requests
-    tickets = [None] * n_requests
-    ready = threading.Semaphore(0)
+    # request k's contents come from its own generator, so several producer
+    # threads build requests ahead of their arrival in any order and the
+    # stream is the same in every run
+    ready, cv = {}, threading.Condition()
+    nxt = [0]
+    consumed = [0]
+    stop = threading.Event()
 
-    def waiter():
-        for k in range(n_requests):
-            ready.acquire()
-            st, ms = srv.wait(tickets[k], timeout_ms=600_000)
-            lat[k] = ms if st == 0 else None
-            done_at[k] = time.perf_counter()
+    def build(k):
+        g = np.random.default_rng([seed, int(rate * 1000), k])
+        n = int(synth.request_sizes(g, 1)[0])
+        idx = g.choice(lib.n_pairs, size=n, replace=n > lib.n_pairs)
+        return idx, logan.HostRequest(lib.request(idx, f"request{k}"), pin=False)
 
-    th = threading.Thread(target=waiter)
-    th.start()
+    def producer():
+        while True:
+            with cv:
+                while not stop.is_set() and nxt[0] - consumed[0] >= 48:
+                    cv.wait(0.05)
+                if stop.is_set():
+                    return
+                k = nxt[0]
+                nxt[0] += 1
+            r = build(k)
+            with cv:
+                ready[k] = r
+                cv.notify_all()
+
+    def take(k):
+        with cv:
+            while k not in ready:
+                cv.wait()
+            consumed[0] += 1
+            cv.notify_all()
+            return ready.pop(k)
+
+    lock = threading.Lock()
+    outstanding = {}   # ticket -> request number
+    done_t, lib_lat, status = {}, {}, {}
+    finished = threading.Event()
+
+    def poller():
+        while True:
+            with lock:
+                items = list(outstanding.items())
+            for tk, k in items:
+                r = srv.poll(tk)
+                if r is not None:
+                    done_t[k] = time.perf_counter()
+                    status[k], lib_lat[k] = r
+                    with lock:
+                        del outstanding[tk]
+            with lock:
+                empty = not outstanding
+            if empty and finished.is_set():
+                return
+            time.sleep(0.001)
+
+    old_switch = sys.getswitchinterval()
+    sys.setswitchinterval(0.0005)  # the submitting thread wakes on time
+    prods = [threading.Thread(target=producer, daemon=True) for _ in range(4)]
+    for t in prods:
+        t.start()
+    pol = threading.Thread(target=poller, daemon=True)
+    pol.start()
+    sub_t, sched_t, reqs = [], [], []
     t0 = time.perf_counter()
-    for k in range(n_requests):
-        delay = t0 + arrivals[k] - time.perf_counter()
+    t_next = t0
+    measured = 0
+    k = 0
+    while True:
+        t_next += rng.exponential(1.0 / rate)
+        in_warmup = t_next - t0 < warmup_s
+        if not in_warmup and (t_next - t0 - warmup_s >= min_s or measured >= min_requests):
+            break
+        idx, h = take(k)
+        delay = t_next - time.perf_counter()
         if delay > 0:
             time.sleep(delay)
         while True:
             try:
-                tickets[k] = srv.submit(pool[which[k]], bufs[k])
+                ts = time.perf_counter()
+                tk = srv.submit(h)
                 break
             except logan.LoganError as e:
                 if e.code != logan.EAGAIN:
                     raise
                 time.sleep(0.001)
-        ready.release()
-    th.join()
-    t_end = max(done_at)
+        with lock:
+            outstanding[tk] = k
+        sub_t.append(ts)
+        sched_t.append(t_next)
+        reqs.append((idx, h.results, h.n_pairs, not in_warmup))
+        del h
+        measured += 0 if in_warmup else 1
+        k += 1
+    finished.set()
+    pol.join()
+    with cv:
+        stop.set()
+        cv.notify_all()
+    for t in prods:
+        t.join()
+    sys.setswitchinterval(old_switch)
+    t_end = max(done_t.values())
     stats = srv.stats()
     srv.close()
-    ok = all(np.array_equal(bufs[k].numpy().view(logan.RESULT_DTYPE).reshape(-1)[:pool[which[k]].n_pairs],
-                            alone[which[k]]) for k in range(n_requests))
-    good = [x for x in lat if x is not None]
-    pairs = int(sum(pool[w].n_pairs for w in which))
-    cells = int(sum(int(alone[w]["cells"].sum()) for w in which))
-    span = t_end - t0
-    return {"rate_req_s": rate, "requests": n_requests, "distinct_requests": distinct,
-            "budget_gb": budget_gb, "inflight": inflight,
-            "p50_ms": float(np.percentile(good, 50)) if good else None,
-            "p99_ms": float(np.percentile(good, 99)) if good else None,
-            "mean_pairs_per_request": pairs / n_requests,
+    meas = [j for j in range(k) if reqs[j][3]]
+    lat_host = np.array([(done_t[j] - sub_t[j]) * 1e3 for j in meas])
+    lat_lib = np.array([lib_lat[j] for j in meas])
+    failed = sum(1 for j in range(k) if status[j] != 0)
+    same = all(np.array_equal(
+        reqs[j][1].numpy().view(logan.RESULT_DTYPE).reshape(-1)[:reqs[j][2]], lib_res[reqs[j][0]])
+        for j in range(k) if status[j] == 0)
+    m0 = min(meas) if meas else 0
+    span = t_end - sub_t[m0] if meas else 1.0
+    pairs = int(sum(reqs[j][2] for j in meas))
+    cells = int(sum(int(lib_res["cells"][reqs[j][0]].sum()) for j in meas))
+    lag = np.array([sub_t[j] - sched_t[j] for j in meas])  # submit behind its arrival time
+    arr_span = (sub_t[meas[-1]] - sub_t[m0]) if len(meas) > 1 else 1.0
+    return {"rate_req_s": rate, "achieved_rate_req_s": (len(meas) - 1) / arr_span if len(meas) > 1 else None,
+            "requests": len(meas), "warmup_requests": k - len(meas), "warmup_s": warmup_s,
+            "distinct_requests": k, "budget_gb": budget_gb, "inflight": inflight,
+            "p50_ms": float(np.percentile(lat_host, 50)) if meas else None,
+            "p99_ms": float(np.percentile(lat_host, 99)) if meas else None,
+            "latency_basis": "host: submit -> completion seen by a poller thread (1 ms sweeps)",
+            "library_p50_ms": float(np.percentile(lat_lib, 50)) if meas else None,
+            "library_p99_ms": float(np.percentile(lat_lib, 99)) if meas else None,
+            "mean_pairs_per_request": pairs / max(1, len(meas)),
             "pairs_per_s": pairs / span, "gcups": cells / span / 1e9,
-            "failed": n_requests - len(good), "peak_arena_gb": stats["peak_bytes"] / (1 << 30),
-            "results_identical_to_alone": bool(ok)}
+            "submit_lag_p99_ms": float(np.percentile(lag, 99) * 1e3) if meas else None,
+            "failed": failed, "peak_arena_gb": stats["peak_bytes"] / (1 << 30),
+            "results_identical_to_alone": bool(same),
+            "requests_from": f"fresh draws of library pairs ({lib.n_pairs} pairs, uneven "
+                             "1 kbp-1 Mbp, X = 50)"}
 
 
 # ---------------------------------------------------------------- CPU oracle
@@ -739,18 +861,34 @@ def main():
     lib_build.build()
     if args.serving_sweep:
         ctx0 = logan.Context(local)
-        for r in [float(x) for x in args.serving_sweep.split(",") if x]:
-            res = serving_run(ctx0, r, args.serving_requests, args.serving_budget_gb,
-                              args.serving_inflight)
-            if rank == 0:
-                print(json.dumps({"serving": res}), flush=True)
+        lib = serving_library(args.serving_library)
+        lib_res = library_results(ctx0, lib)
+        budgets = [float(x) for x in args.serving_budgets.split(",") if x] or \
+            [args.serving_budget_gb]
+        for bud in budgets:
+            for r in [float(x) for x in args.serving_sweep.split(",") if x]:
+                res = serving_run(ctx0, lib, lib_res, r, bud, args.serving_inflight,
+                                  warmup_s=args.serving_warmup, min_s=args.serving_seconds,
+                                  min_requests=args.serving_requests)
+                if rank == 0:
+                    print(json.dumps({"serving": res}), flush=True)
         ctx0.close()
         return
-    b = workload(args.workload, args.pairs, rank)
+    sharded = args.shard == "lpt" and world > 1
+    b = workload(args.workload, args.pairs, 0 if sharded else rank)
+    if sharded:
+        # every rank builds the same batch and keeps its LPT share of the pairs
+        full_batch = b
+        shard_idx = shard.shard_indices(b, world, rank)
+        b = shard.shard_batch(b, shard_idx)
     packed = bool(b.meta["packed2bit"])
     A, B, S, Xs = logan.batch_to_device(b, packed2bit=packed, device=f"cuda:{local}")
     ctx = logan.Context(local)
     ctx.set_option(logan.OPT_CONCURRENT, args.concurrent)
+    if args.long_item is not None:
+        ctx.set_option(logan.OPT_LONG_ITEM, args.long_item)
+    if args.packed16 is not None:
+        ctx.set_option(logan.OPT_PACKED16, args.packed16)
     stream = torch.cuda.Stream()
     ws = ctx.workspace(A, B, b.n_pairs)
     out = torch.empty((b.n_pairs, 10), dtype=torch.int32, device=f"cuda:{local}")
@@ -845,15 +983,25 @@ def main():
     peak = logan.intpeak(local, 1, 2000)[0] / 1e9
     achieved = OPS_PER_CELL * dom_cells / (level_ms[dom] * 1e-3) / 1e9 if level_ms[dom] > 0 else 0.0
 
+    cfg = workload_config(b, args.workload, args.pairs)
+    if sharded:
+        cfg["parallelism"] = (f"one batch split over {world} ranks by LPT over pair lengths "
+                              "(no collective on the data path; results gathered on the host)")
+        full = shard.gather_results(res, shard_idx, full_batch.n_pairs)
+        ok_all = bool(np.all(full["status"] == 0))
     line = {"metric": METRIC, "value": value, "unit": "GCUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
-            "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+            "higher_is_better": True, "scaling": "strong" if sharded else "weak",
+            "vs_baseline": None,
             "dtype": "int32", "data": "synthetic",
-            "config": workload_config(b, args.workload, args.pairs),
+            "config": cfg,
             "clocks": clocks, "gpu_launches": launches * args.steps,
             "cells_per_step": tot_cells,
             "levels": {"ms": [round(float(v), 4) for v in level_ms],
                        "items": last["items"], "cells": last["cells"]}}
+    if sharded:
+        line["shard"] = {"pairs_this_rank": int(b.n_pairs), "pairs_total": int(full_batch.n_pairs),
+                         "gathered_all_ok": ok_all}
     if step in step_stats:
         med, best = step_stats[step]
         line["step_ms"] = {"median": med, "best": best,
@@ -1013,8 +1161,12 @@ def main():
                 "serial_ms_per_step": ms_serial})
 
     if not args.no_serving and args.workload == "lognormal_batch":
-        line["serving"] = serving_run(ctx, args.serving_rate, args.serving_requests,
-                                      args.serving_budget_gb, args.serving_inflight)
+        # a short run of the serving stream for the headline line (the
+        # --serving-sweep mode runs each point for 60 s or 2,000 requests)
+        lib = serving_library(args.serving_line_library)
+        line["serving"] = serving_run(ctx, lib, library_results(ctx, lib), args.serving_rate,
+                                      args.serving_budget_gb, args.serving_inflight,
+                                      warmup_s=2.0, min_s=8.0, min_requests=600)
         line["metric_serving"] = {"p50_ms": line["serving"]["p50_ms"],
                                   "p99_ms": line["serving"]["p99_ms"],
                                   "at_rate_req_s": args.serving_rate}

@@ -179,9 +179,11 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   bytes), out, stream: as logan_extend_batch.
  * Per pair, max(|match|, |mismatch|, |gap_open| + |gap_extend|) * (m + n)
  * + X must stay below 2^29 (else LOGAN_EINVAL for the pair).  Bands are
- * held in windows of 64, 128, 256 and 512 rows (the first by X: <= 35, <= 150,
- * <= 300, larger); a pair whose band outgrows 512 rows, or whose X exceeds
- * 2^20 - 4096, gets status LOGAN_ERANGE.  Runs on
+ * held in register windows of 64, 128, 256 and 512 rows (the first by X:
+ * <= 35, <= 150, <= 300, larger); a band that outgrows 512 rows, or an X
+ * above 2^20 - 4096, continues in a device-memory ring of half the
+ * workspace ring's width (2^LOGAN_OPT_RING_CAP / 2 rows: 32,768 by
+ * default); only a band wider than that gets status LOGAN_ERANGE.  Runs on
  * `stream` (no graphs, no timing statistics).  Returns LOGAN_EINVAL for
  * invalid scalars or pointers, LOGAN_ENOMEM if ws_bytes is too small,
  * LOGAN_ECUDA on a launch failure.
@@ -189,6 +191,42 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
 int logan_extend_batch_affine(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                               const logan_seqs_t *seqsB, const logan_seed_t *seeds,
                               uint32_t n_pairs, int32_t match, int32_t mismatch,
+                              int32_t gap_open, int32_t gap_extend, int32_t X,
+                              const int32_t *X_per_pair, void *workspace, size_t ws_bytes,
+                              logan_result_t *out, void *stream);
+
+/*
+ * Seeded X-drop extension of sequences over any alphabet of K <= 32 letters,
+ * scored by a K x K substitution matrix, with affine gaps (protein and other
+ * scoring schemes are the paper's future work, Sec. VIII; the sweep, X-drop
+ * rule, band trimming, best cell, split at the seed and result fields are
+ * those of logan_extend_batch, with the Gotoh states of
+ * logan_extend_batch_affine and matrix[a * K + b] in place of
+ * match / mismatch).
+ *   seqsA, seqsB: device pools of LETTER CODES, one byte each, values 0..K-1
+ *       (packed2bit must be 0; pool_bases is not used); a sequence holding a
+ *       code >= K makes its pairs LOGAN_EINVAL.
+ *   seeds, n_pairs, X, X_per_pair, out, stream: as logan_extend_batch; the
+ *       seed score is the sum of matrix[A[posA+t] * K + B[posB+t]].
+ *   matrix: HOST pointer, K * K int32 row-major, row = letter of A, column =
+ *       letter of B, |entry| <= 1000 (copied on `stream` before use).
+ *   gap_open, gap_extend: -1000 <= v <= 0 (gap_open = 0: linear gaps).
+ *   workspace: device, 256-byte aligned, at least
+ *       logan_matrix_workspace_size bytes; caller-owned.
+ * Per pair, max(max|entry|, |gap_open| + |gap_extend|) * (m + n) + X must
+ * stay below 2^29 (else LOGAN_EINVAL for the pair).  Every extension runs in
+ * one block of 256 threads over a device-memory ring of
+ * 2^LOGAN_MATRIX_RING_LOG2 rows; a wider band gets LOGAN_ERANGE.  Returns
+ * LOGAN_EINVAL for invalid scalars or pointers (K outside 1..32, an entry
+ * out of range, packed pools), LOGAN_ENOMEM if ws_bytes is too small,
+ * LOGAN_ECUDA on a launch failure.
+ */
+#define LOGAN_MATRIX_RING_LOG2 14
+int logan_matrix_workspace_size(const logan_ctx_t *ctx, const logan_seqs_t *seqsA,
+                                const logan_seqs_t *seqsB, uint32_t n_pairs, size_t *bytes);
+int logan_extend_batch_matrix(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
+                              const logan_seqs_t *seqsB, const logan_seed_t *seeds,
+                              uint32_t n_pairs, const int32_t *matrix, int K,
                               int32_t gap_open, int32_t gap_extend, int32_t X,
                               const int32_t *X_per_pair, void *workspace, size_t ws_bytes,
                               logan_result_t *out, void *stream);
@@ -371,6 +409,7 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   LOGAN_OPT_MIGRATION_MB  band-state migration budget (below)
  *   LOGAN_OPT_CONCURRENT    concurrent start levels (below)
  *   LOGAN_OPT_LONG_ITEM     latency forms for long items (below)
+ *   LOGAN_OPT_PACKED16      packed 16-bit level kernels (below)
  */
 #define LOGAN_OPT_GRAPHS 1
 #define LOGAN_OPT_TIMING 2
@@ -400,6 +439,19 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                                     has at most 32 items per SM, else
                                     m + n >= 65536.  Results never depend on
                                     it. */
+#define LOGAN_OPT_PACKED16 11    /* 1 (default): a window level that has a
+                                    packed form (two 16-bit cells per 32-bit
+                                    register) runs it when the call's scoring
+                                    and X provably fit 16 bits -- for a window
+                                    of W rows, W * (Xmax + 2*max(match,0) +
+                                    |gap| + 2) <= 32767 and W * (|mismatch| +
+                                    |gap| + 2*max(match,0) + 2) <= 16383, Xmax
+                                    the largest X that can reach the level
+                                    (the scalar X, or the X-class bounds of
+                                    the start-level table when X is per pair
+                                    or a start level is forced); otherwise,
+                                    or with 0, the 32-bit form.  Results are
+                                    identical either way. */
 int logan_set_option(logan_ctx_t *ctx, int option, int64_t value);
 int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
 
@@ -432,6 +484,8 @@ typedef struct {
     uint32_t items[LOGAN_MAX_LEVELS + 1];
     uint64_t cells[LOGAN_MAX_LEVELS + 1];
     uint32_t launches;
+    uint32_t packed_levels;  /* bit k: window level k ran in its packed
+                                16-bit form (LOGAN_OPT_PACKED16) */
 } logan_stats_t;
 int logan_last_stats(logan_ctx_t *ctx, logan_stats_t *stats);
 /* The same for an earlier timed call: back = 0 is the last one, up to 31. */

@@ -1,7 +1,9 @@
 """CPU oracle for batched X-drop seed extension -- TEST INFRASTRUCTURE ONLY.
 
-Loads ``xdrop_oracle.c`` (linear gaps, the paper's method) and
-``xdrop_affine_oracle.c`` (the same extension with affine gaps) compiled
+Loads ``xdrop_oracle.c`` (linear gaps, the paper's method),
+``xdrop_affine_oracle.c`` (the same extension with affine gaps),
+``xdrop_traceback_oracle.c`` (alignment paths) and ``xdrop_matrix_oracle.c``
+(any alphabet scored by a substitution matrix, affine gaps), compiled
 with the host C compiler into ``oracle/_build/liboracle.so`` through ctypes.  Only the tests, the smoke
 check and the CPU-baseline leg of ``bench.py`` may use it; the library and
 its Python binding never import it.  It shares no code with the CUDA path.
@@ -25,6 +27,7 @@ _HERE = os.path.dirname(os.path.abspath(__file__))
 _SRC = os.path.join(_HERE, "xdrop_oracle.c")
 _SRC_AFFINE = os.path.join(_HERE, "xdrop_affine_oracle.c")
 _SRC_TRACE = os.path.join(_HERE, "xdrop_traceback_oracle.c")
+_SRC_MATRIX = os.path.join(_HERE, "xdrop_matrix_oracle.c")
 _BUILD = os.path.join(_HERE, "_build")
 _LIB_PATH = os.path.join(_BUILD, "liboracle.so")
 
@@ -46,10 +49,11 @@ def build(force: bool = False) -> str:
     if force or not os.path.exists(_LIB_PATH) or \
             os.path.getmtime(_LIB_PATH) < max(os.path.getmtime(_SRC),
                                               os.path.getmtime(_SRC_AFFINE),
-                                              os.path.getmtime(_SRC_TRACE)):
+                                              os.path.getmtime(_SRC_TRACE),
+                                              os.path.getmtime(_SRC_MATRIX)):
         tmp = _LIB_PATH + f".{os.getpid()}.tmp"
         subprocess.check_call(["gcc", "-O2", "-std=c11", "-shared", "-fPIC", "-pthread",
-                               "-o", tmp, _SRC, _SRC_AFFINE, _SRC_TRACE])
+                               "-o", tmp, _SRC, _SRC_AFFINE, _SRC_TRACE, _SRC_MATRIX])
         os.replace(tmp, _LIB_PATH)
     return _LIB_PATH
 
@@ -90,6 +94,16 @@ def lib():
         L.oracle_pair_traceback.argtypes = [p, i64, p, i64, i64, i64, i64, i64, i64, i64, i64, p,
                                             pi64]
         L.oracle_pair_traceback.restype = ctypes.c_int
+        L.oracle_matrix_extend.argtypes = [p, i64, p, i64, p, i64, i64, i64, i64,
+                                           ctypes.POINTER(_Ext)]
+        L.oracle_matrix_extend.restype = ctypes.c_int
+        L.oracle_matrix_pair.argtypes = [p, i64, p, i64, i64, i64, i64, p, i64, i64, i64, i64, p]
+        L.oracle_matrix_pair.restype = ctypes.c_int
+        L.oracle_matrix_batch.argtypes = [p, p, p, ctypes.c_uint32, p, p, p, ctypes.c_uint32,
+                                          p, i64, p, i64, i64, i64, i64, p, ctypes.c_int, p]
+        L.oracle_matrix_batch.restype = ctypes.c_int
+        L.oracle_matrix_params_valid.argtypes = [p, i64, i64, i64, i64]
+        L.oracle_matrix_params_valid.restype = ctypes.c_int
         _lib = L
     return _lib
 
@@ -249,3 +263,67 @@ def pair_traceback(A: bytes, B: bytes, posA: int, posB: int, k: int, match: int 
     if rc:
         raise ValueError("invalid pair or allocation failure")
     return buf.raw[:n.value].decode()
+
+
+# ---- substitution matrix, any alphabet (xdrop_matrix_oracle.c) ----
+
+def _matrix(M):
+    M = np.ascontiguousarray(M, dtype=np.int32)
+    if M.ndim != 2 or M.shape[0] != M.shape[1]:
+        raise ValueError("the substitution matrix must be K x K")
+    return M, M.shape[0]
+
+
+def matrix_extend(a: bytes, b: bytes, M, gap_open: int = 0, gap_extend: int = -1, X: int = 50):
+    """One X-drop extension of letter codes a against b (bytes of values
+    0..K-1), scored by the K x K matrix M and affine gaps.
+    Returns (best, bi, bj, cells)."""
+    M, K = _matrix(M)
+    out = _Ext()
+    rc = lib().oracle_matrix_extend(_buf(a), len(a), _buf(b), len(b), M.ctypes.data, K,
+                                    gap_open, gap_extend, X, ctypes.byref(out))
+    if rc:
+        raise MemoryError("oracle extension could not allocate")
+    return out.best, out.bi, out.bj, out.cells
+
+
+def matrix_pair(A: bytes, B: bytes, posA: int, posB: int, k: int, M, gap_open: int = 0,
+                gap_extend: int = -1, X: int = 50) -> np.void:
+    M, K = _matrix(M)
+    r = np.zeros(1, dtype=PAIR_DTYPE)
+    lib().oracle_matrix_pair(_buf(A), len(A), _buf(B), len(B), posA, posB, k, M.ctypes.data, K,
+                             gap_open, gap_extend, X, r.ctypes.data)
+    return r[0]
+
+
+def matrix_params_valid(M, gap_open: int, gap_extend: int, X: int) -> bool:
+    M, K = _matrix(M)
+    return bool(lib().oracle_matrix_params_valid(M.ctypes.data, K, gap_open, gap_extend, X))
+
+
+def run_batch_matrix(b, M, gap_open: int, gap_extend: int, threads: Optional[int] = None):
+    """Every pair of a synth.Batch-like object whose pools hold letter codes
+    (one byte each, values < K), scored by M with affine gaps (b.match,
+    b.mismatch and b.gap are ignored).  Returns (PAIR_DTYPE results, threads)."""
+    M, K = _matrix(M)
+    poolA = np.ascontiguousarray(b.poolA, dtype=np.uint8)
+    poolB = np.ascontiguousarray(b.poolB, dtype=np.uint8)
+    offA = np.ascontiguousarray(b.offA, dtype=np.uint64)
+    offB = np.ascontiguousarray(b.offB, dtype=np.uint64)
+    lenA = np.ascontiguousarray(b.lenA, dtype=np.uint32)
+    lenB = np.ascontiguousarray(b.lenB, dtype=np.uint32)
+    sd = np.ascontiguousarray(
+        np.stack([b.seeds[f] for f in ("idxA", "idxB", "posA", "posB", "len")], axis=1)
+        .astype(np.uint32))
+    n = sd.shape[0]
+    out = np.zeros(n, dtype=PAIR_DTYPE)
+    xs = None if b.Xs is None else np.ascontiguousarray(b.Xs, dtype=np.int32)
+    if threads is None:
+        threads = os.cpu_count() or 1
+    used = lib().oracle_matrix_batch(poolA.ctypes.data, offA.ctypes.data, lenA.ctypes.data,
+                                     lenA.size, poolB.ctypes.data, offB.ctypes.data,
+                                     lenB.ctypes.data, lenB.size, sd.ctypes.data, n,
+                                     M.ctypes.data, K, gap_open, gap_extend, b.X,
+                                     None if xs is None else xs.ctypes.data, int(threads),
+                                     out.ctypes.data)
+    return out, used

@@ -68,6 +68,10 @@ struct logan_ctx {
     // LOGAN_OPT_LONG_ITEM: m + n from which items of levels < kTwinLevels
     // take the latency form; -1 never, -2 automatic
     int64_t long_item = -2;
+    // LOGAN_OPT_PACKED16: 1 = run a level in its packed 16-bit form when the
+    // call's scoring and X provably fit (see packed16_levels), 0 = never
+    int64_t packed16 = 1;
+    int packed_blocks_per_sm[kNumLevels] = {};
     int8_t next_level[kNumLevels] = {};
     // timing: the events of the last kEvSets timed calls (ring)
     cudaEvent_t evs[kEvSets][kEvPerSet] = {};
@@ -80,6 +84,7 @@ struct logan_ctx {
         uint32_t p1_levels = 0;  // bit u: phase-1 events of launch unit u recorded
         uint32_t p2_levels = 0;
         bool plain = false;
+        uint32_t packed = 0;     // bit l: level l ran in its packed 16-bit form
     } calls[kEvSets];
     // the level counters of each timed call, copied back at its end
     Counters* hcounters = nullptr;  // pinned, kEvSets entries
@@ -205,9 +210,13 @@ void default_table(LevelTable& t) {
     t.only_xclass = -1;
 }
 
-int launch_unit(logan_ctx* c, int u, const KernelArgs& ka, int phase, cudaStream_t s) {
+int launch_unit(logan_ctx* c, int u, const KernelArgs& ka, int phase, cudaStream_t s,
+                uint32_t packed) {
     cudaError_t e;
-    if (u >= kNumLevels) {
+    if (u < kNumLevels && ((packed >> u) & 1u)) {
+        const int grid = c->num_sms * std::max(1, c->packed_blocks_per_sm[u]);
+        e = launch_packed_level_persistent(u, ka, grid, phase, s);
+    } else if (u >= kNumLevels) {
         const int l = u - kNumLevels;
         const int grid = c->num_sms * std::max(1, c->twin_blocks_per_sm[l]);
         e = launch_twin_persistent(l, ka, grid, phase, s);
@@ -249,6 +258,40 @@ AuxSet* aux_for(logan_ctx* c, cudaStream_t s) {
     }
     c->aux.push_back(a);
     return &c->aux.back();
+}
+
+// Levels that run in their packed 16-bit form in this call: those with a
+// packed kernel whose window W satisfies
+//   W * (Xmax + 2*max(match,0) + |gap| + 2) <= 32767  and
+//   W * (|mismatch| + |gap| + 2*max(match,0) + 2) <= 16383,
+// Xmax the largest X that can reach the level: the scalar X when there is
+// no per-pair X and no forced start level, else the upper bound of every X
+// class whose start level is at or below it (items only move to wider
+// levels).  These bounds keep every 16-bit half inside [0, 65536) through
+// the kernel's additions (xdrop_group16.cu).
+uint32_t packed16_levels(const logan_ctx* c, Scoring sc, int32_t X, const int32_t* Xs,
+                         const LevelTable& tab, int64_t force) {
+    if (!c->packed16) return 0u;
+    static const int64_t upper[kXClasses] = {15, 35, 75, 150, 300, 700, 2000, int64_t(1) << 29};
+    const int64_t mp = std::max<int64_t>(sc.match, 0);
+    const int64_t ag = -int64_t(sc.gap), am = sc.mismatch < 0 ? -int64_t(sc.mismatch) : sc.mismatch;
+    uint32_t mask = 0u;
+    for (int l = 0; l < kWarpLevels; ++l) {
+        if (!packed_level(l) || l > tab.max_level) continue;
+        int64_t xmax = 0;
+        if (!Xs && force < 0) {
+            xmax = X;
+        } else if (force >= 0) {
+            xmax = force <= l ? (Xs ? upper[kXClasses - 1] : X) : 0;
+        } else {
+            for (int k = 0; k < kXClasses; ++k)
+                if (tab.lv[k] <= l) xmax = std::max(xmax, upper[k]);
+        }
+        const int64_t W = level_window(l);
+        if (W * (xmax + 2 * mp + ag + 2) <= 32767 && W * (am + ag + 2 * mp + 2) <= 16383)
+            mask |= 1u << l;
+    }
+    return mask;
 }
 
 // The whole pipeline on `s` (no synchronisation).  plain != 0: one-launch
@@ -346,12 +389,15 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     ka.sc = sc;
     ka.one = 1;
     for (int k = 0; k < 16; ++k) ka.pw[k] = 1u << (31 - 2 * k);
+    for (int k = 0; k < 16; ++k) ka.pw16[k] = 1u << (15 - k);
     for (int l = 0; l < kNumLevels; ++l) {
         ka.next_level[l] = c->next_level[l];
         ka.mig_cap[l] = L.mig_cap[l];
         ka.mig_pool[l] = L.mig_cap[l] ? reinterpret_cast<int32_t*>(ws + L.mig_pool[l]) : nullptr;
     }
     ka.mig_slot = reinterpret_cast<int32_t*>(ws + L.mig_slot);
+    const int64_t forced = c->force_level >= 0 ? std::min<int64_t>(c->force_level, maxl) : -1;
+    const uint32_t packed = (aff || plain) ? 0u : packed16_levels(c, sc, X, Xs, tab, forced);
     if (aff) {
         // affine levels, narrowest first (each receives the bands that
         // outgrew the previous one), then the rejected items, then combine
@@ -361,7 +407,8 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
                 return LOGAN_ECUDA;
             ++launches;
         }
-        if (launch_affine_reject(ka, kWarpLevels, s) != cudaSuccess ||
+        if (launch_affine_ring(ka, kWarpLevels, aff->open, aff->extend, int(L.ring_slots),
+                               s) != cudaSuccess ||
             launch_combine(seeds, info, ext, n_pairs, out, s) != cudaSuccess)
             return LOGAN_ECUDA;
         c->launches_last = launches + 2;
@@ -394,7 +441,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
             cudaStream_t st = ax ? ax->st[u] : s;
             if (ax && cudaStreamWaitEvent(st, ax->fork, 0) != cudaSuccess) return LOGAN_ECUDA;
             if (!rec(EV_P1S + u, st)) return LOGAN_ECUDA;
-            if (launch_unit(c, u, ka, PHASE_INITIAL, st) != LOGAN_OK) return LOGAN_ECUDA;
+            if (launch_unit(c, u, ka, PHASE_INITIAL, st, packed) != LOGAN_OK) return LOGAN_ECUDA;
             if (!rec(EV_P1E + u, st)) return LOGAN_ECUDA;
             if (ax && (cudaEventRecord(ax->join[u], st) != cudaSuccess ||
                        cudaStreamWaitEvent(s, ax->join[u], 0) != cudaSuccess))
@@ -409,7 +456,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         for (int u : {lvl, lvl < kTwinLevels && !plain ? kNumLevels + lvl : -1}) {
             if (u < 0) continue;
             if (!rec(EV_P2S + u, s)) return LOGAN_ECUDA;
-            if (launch_unit(c, u, ka, PHASE_ESCALATED, s) != LOGAN_OK) return LOGAN_ECUDA;
+            if (launch_unit(c, u, ka, PHASE_ESCALATED, s, packed) != LOGAN_OK) return LOGAN_ECUDA;
             if (!rec(EV_P2E + u, s)) return LOGAN_ECUDA;
             p2_levels |= 1u << u;
             ++launches;
@@ -434,6 +481,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         ci.p1_levels = p1_levels;
         ci.p2_levels = p2_levels;
         ci.plain = plain != 0;
+        ci.packed = packed;
         c->timed_calls += 1;
         c->timing_pending = true;
     }
@@ -467,7 +515,7 @@ int extend_common(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         uint64_t(uintptr_t(seeds)), uint64_t(uintptr_t(out)), uint64_t(uintptr_t(ws)),
         uint64_t(uintptr_t(stream)), uint64_t(c->force_level), uint64_t(c->max_level),
         uint64_t(c->ring_log2), uint64_t(c->plain_level), uint64_t(c->mig_mb),
-        uint64_t(c->concurrent), uint64_t(c->long_item)};
+        uint64_t(c->concurrent), uint64_t(c->long_item), uint64_t(c->packed16)};
     for (const logan_seqs_t* p : {A, B}) {
         key.push_back(uint64_t(uintptr_t(p->bases)));
         key.push_back(uint64_t(uintptr_t(p->offsets)));
@@ -589,6 +637,8 @@ int logan_ctx_create(logan_ctx_t** out, int device, const char* autotune_json) {
     for (int l = 0; l < kNumLevels; ++l) c->next_level[l] = int8_t(l + 1);
     for (int l = 0; l < kNumLevels; ++l)
         c->blocks_per_sm[l] = l < kWarpLevels ? warp_level_blocks_per_sm(l) : cta_level_blocks_per_sm(l);
+    for (int l = 0; l < kNumLevels; ++l)
+        c->packed_blocks_per_sm[l] = packed_level(l) ? packed_level_blocks_per_sm(l) : 0;
     for (int l = 0; l < kTwinLevels; ++l) c->twin_blocks_per_sm[l] = twin_blocks_per_sm(l);
     for (int l = 0; l < affine_levels(); ++l) c->affine_blocks_per_sm[l] = affine_blocks_per_sm(l);
     for (auto& set : c->evs)
@@ -712,6 +762,7 @@ int logan_set_option(logan_ctx_t* c, int option, int64_t v) {
             if (v < -2) return LOGAN_EINVAL;
             c->long_item = v;
             return LOGAN_OK;
+        case LOGAN_OPT_PACKED16: c->packed16 = v ? 1 : 0; return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }
@@ -729,6 +780,7 @@ int logan_get_option(const logan_ctx_t* c, int option, int64_t* v) {
         case LOGAN_OPT_MIGRATION_MB: *v = c->mig_mb; return LOGAN_OK;
         case LOGAN_OPT_CONCURRENT: *v = c->concurrent; return LOGAN_OK;
         case LOGAN_OPT_LONG_ITEM: *v = c->long_item; return LOGAN_OK;
+        case LOGAN_OPT_PACKED16: *v = c->packed16; return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }
@@ -779,6 +831,7 @@ int logan_call_stats(logan_ctx_t* c, int back, logan_stats_t* st) {
         st->cells[l] = h.cells[l];
     }
     st->launches = ci.launches;
+    st->packed_levels = ci.packed;
     return LOGAN_OK;
 }
 

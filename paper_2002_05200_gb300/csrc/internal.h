@@ -29,6 +29,9 @@ struct KernelArgs {
     // pw[k] = 2^(31 - 2k): multiplying a 2-bit-per-row flag word by it moves
     // row k's flag to the sign bit (a multiply-add, FMA pipe)
     uint32_t pw[16];
+    // pw16[h] = 2^(15 - h): moves bits h and h + 16 of a row mask to bits 15
+    // and 31 (the halves' top bits) as a multiply-add
+    uint32_t pw16[16];
     // level an item goes to when its band outgrows level k (kNumLevels = ring)
     int8_t next_level[kNumLevels];
     // migration records written by level k (nullptr or cap 0: restart instead)
@@ -66,6 +69,12 @@ cudaError_t launch_warp_level_persistent(int level, const KernelArgs& ka, int gr
                                          cudaStream_t s);
 cudaError_t launch_warp_level_plain(int level, const KernelArgs& ka, cudaStream_t s);
 int warp_level_blocks_per_sm(int level);
+// packed 16-bit form of a register level (xdrop_group16.cu): same queues,
+// results and band-state records as the level's 32-bit kernel
+bool packed_level(int level);
+cudaError_t launch_packed_level_persistent(int level, const KernelArgs& ka, int grid, int phase,
+                                           cudaStream_t s);
+int packed_level_blocks_per_sm(int level);
 // level k's one-warp form (k < kTwinLevels), persistent over twin_queue(k)
 cudaError_t launch_twin_persistent(int level, const KernelArgs& ka, int grid, int phase,
                                    cudaStream_t s);
@@ -78,7 +87,11 @@ int affine_levels();
 int affine_blocks_per_sm(int level);
 cudaError_t launch_affine_level(int level, const KernelArgs& ka, int gap_open, int gap_extend,
                                 int grid, cudaStream_t s);
-cudaError_t launch_affine_reject(const KernelArgs& ka, int queue, cudaStream_t s);
+// bands that outgrow the affine windows, and X too large for their keys:
+// every entry of queue q continues in the device-memory ring kernel
+// (xdrop_matrix.cu) with half the workspace ring's width
+cudaError_t launch_affine_ring(const KernelArgs& ka, int q, int go, int ge, int grid,
+                               cudaStream_t s);
 
 // pre/post-processing kernels (prep.cu)
 struct PoolDev {

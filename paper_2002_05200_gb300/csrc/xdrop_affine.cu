@@ -18,7 +18,9 @@
 // Levels: 64 rows (8 lanes x 8, four extensions per warp), 128 (8 x 16,
 // four per warp), 256 (16 x 16, two per warp) and 512 (32 x 16); an item
 // starts at the level its X class maps to, a band that outgrows a window
-// restarts at the next one, and one outgrowing 512 rows gets LOGAN_ERANGE.
+// restarts at the next one, and one outgrowing 512 rows (or an X too large
+// for the keys) continues in the device-memory ring kernel of
+// xdrop_matrix.cu, which has no width limit below the workspace ring.
 #include "internal.h"
 
 #include "../../include/logan.h"
@@ -101,12 +103,13 @@ __device__ __forceinline__ void a_finish(const KernelArgs& ka, const AState& u, 
     r.status = 0;
     r.cells = 0ull;
     if (u.overflow) {
-        if (level + 1 < n_levels) {
-            const unsigned int t = atomicAdd(&ka.counters->tail[level + 1], 1u);
-            ka.queues[size_t(level + 1) * ka.qcap + t] = u.item;
-            return;
-        }
-        r.status = LOGAN_ERANGE;
+        // the next window, or after the widest one the device-memory ring
+        // (queue kWarpLevels, which also holds the items whose X is too
+        // large for these keys)
+        const int nq = level + 1 < n_levels ? level + 1 : kWarpLevels;
+        const unsigned int t = atomicAdd(&ka.counters->tail[nq], 1u);
+        ka.queues[size_t(nq) * ka.qcap + t] = u.item;
+        return;
     } else {
         r.best = u.best;
         r.bi = u.bi;
@@ -342,20 +345,6 @@ __global__ void __launch_bounds__(128, 4) k_affine(KernelArgs ka, int go, int ge
     }
 }
 
-// items whose X is too large for the affine keys: LOGAN_ERANGE
-__global__ void k_affine_reject(KernelArgs ka, int queue) {
-    const unsigned int n = ka.counters->started[queue];
-    for (unsigned int s = blockIdx.x * blockDim.x + threadIdx.x; s < n; s += gridDim.x * blockDim.x) {
-        ExtRes r;
-        r.best = 0;
-        r.bi = 0;
-        r.bj = 0;
-        r.status = LOGAN_ERANGE;
-        r.cells = 0ull;
-        ka.ext[ka.queues[size_t(queue) * ka.qcap + s]] = r;
-    }
-}
-
 #define LOGAN_AFFINE_LEVELS(X) X(0, 8, 8) X(1, 8, 16) X(2, 16, 16) X(3, 32, 16)
 constexpr int kAffineLevels = 4;
 
@@ -385,11 +374,6 @@ cudaError_t launch_affine_level(int level, const KernelArgs& ka, int go, int ge,
 #undef CASE
         default: return cudaErrorInvalidValue;
     }
-    return cudaGetLastError();
-}
-
-cudaError_t launch_affine_reject(const KernelArgs& ka, int queue, cudaStream_t s) {
-    k_affine_reject<<<64, 256, 0, s>>>(ka, queue);
     return cudaGetLastError();
 }
 

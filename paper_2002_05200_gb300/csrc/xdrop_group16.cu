@@ -1,0 +1,580 @@
+// X-drop extension with G-lane units and the band packed two rows to a
+// 32-bit register (16-bit SIMD), for window levels whose score range
+// provably fits 16 bits.
+//
+// Method: the paper's recurrence and X-drop rule (Sec. III-A), the
+// anti-diagonal sweep of Algorithm 1 with the cell update of Algorithm 2,
+// and the per-anti-diagonal maximum of Sec. IV-A -- the same computation as
+// the 32-bit G-lane kernel (xdrop_group.cu), with the same results.
+//
+// Layout.  Lane g of a unit owns window rows g*32 + k, k < 32; register h
+// (h < 16) holds rows h (low half) and h + 16 (high half).  So the "up" and
+// "diag" predecessors of register h are register h - 1 of the same lane
+// (both halves move together), and only register 0 needs the neighbour
+// lane's top row (one shuffle and one byte permute per anti-diagonal).
+//
+// Values.  A cell at window row r of anti-diagonal e holds
+//     sigma = 32768 + u*W + (W - 1 - r),   u = S - T_e,  T_e = best_{<e} - X,
+// when it is live (u >= 0, i.e. sigma >= 32768, bit 15 set), and DEAD =
+// 16384 otherwise.  The low log2(W) bits are the row code, so one unsigned
+// 16-bit maximum over a unit gives the anti-diagonal's best score and, for
+// equal scores, its smallest row (the tie-break of the 32-bit kernel's
+// keyed max).  Every candidate is re-based onto the cell's own row code:
+// "up" and "diag" come from row r - 1 (code + 1) and get -1, "left" from the
+// same row.  The host enables this kernel only when
+//     W*(Xmax + 2*max(match,0) + |gap| + 2) <= 32767   and
+//     W*(|mismatch| + |gap| + 2*max(match,0) + 2) <= 16383,
+// Xmax the largest X that can reach the level.  Then every half-word stays
+// inside [0, 65536) through every addition, so the additions are plain
+// 32-bit multiply-adds of both halves at once (FMA pipe, no carry or borrow
+// between halves), a dead value never climbs to 32768 within the two steps
+// it is read, and the only per-half operations are one 3-input 16-bit DPX
+// maximum and the bit tests of the prune (ALU pipe).
+//
+// Range and prune: a cell outside the anti-diagonal's range [rlo, rhi] or
+// with sigma < 32768 is stored as DEAD (the range bit of the row is moved to
+// the half's bit 15 by a multiply, ANDed with the value, and a byte permute
+// with sign replication turns bit 15 of each half into a half-word mask).
+//
+// Everything else -- the b' shift register fed by a per-unit prefetch,
+// window slides at the loop top (here by half a lane, 16 rows), band-state
+// records for the next level (32-bit relative scores, the same records the
+// 32-bit levels write and read), persistent queue pops -- follows the
+// 32-bit kernel.  Codes are kept as two bit planes per lane (bit r = row r),
+// so a row's match flag is one bit of ~((a0 ^ b0) | (a1 ^ b1)).
+#include "internal.h"
+
+namespace logan {
+
+namespace {
+
+constexpr uint32_t FULL = 0xffffffffu;
+constexpr uint32_t LIVE = 0x8000u;
+constexpr uint32_t DEAD2 = 0x40004000u;  // DEAD in both halves
+constexpr int NEGU = -(1 << 20);         // -inf of the 32-bit relative records
+
+template <int G>
+struct P16 {
+    static constexpr int C = 32;  // rows per lane (16 registers per anti-diagonal)
+    static constexpr int W = G * C;
+    static constexpr int LOG2W = W == 32 ? 5 : W == 64 ? 6 : W == 128 ? 7 : W == 256 ? 8 : 9;
+    static constexpr int PREFETCH = 16 * G;
+    static_assert((1 << LOG2W) == W, "window must be a power of two");
+    // the substitution step multiplies a match flag at bit h' < 8 by
+    // (match - mismatch) * W >> h', exact only for W >= 128
+    static_assert(W >= 128, "packed levels need a window of at least 128 rows");
+};
+
+struct S16 {
+    int base, lo, hi, d;
+    int best, T, T1, T2;
+    int bi, bj;
+    int m, n, X;
+    unsigned long long cells, cells0;
+    int64_t apos, bpos;
+    int dir;
+    int q0;
+    uint32_t bpre;
+    uint32_t item;
+    bool active, done, overflow, migrated;
+    uint32_t a0, a1, b0, b1;  // code bit planes of the lane's 32 rows
+};
+
+// 16 two-bit codes (code t at bits 2t) -> their low and high bit planes
+// (bit t of each).
+__device__ __forceinline__ void planes16(uint32_t c, uint32_t& p0, uint32_t& p1) {
+    uint32_t x = c & 0x55555555u, y = (c >> 1) & 0x55555555u;
+    x = (x | (x >> 1)) & 0x33333333u;
+    y = (y | (y >> 1)) & 0x33333333u;
+    x = (x | (x >> 2)) & 0x0f0f0f0fu;
+    y = (y | (y >> 2)) & 0x0f0f0f0fu;
+    x = (x | (x >> 4)) & 0x00ff00ffu;
+    y = (y | (y >> 4)) & 0x00ff00ffu;
+    p0 = (x | (x >> 8)) & 0xffffu;
+    p1 = (y | (y >> 8)) & 0xffffu;
+}
+
+// stream codes q..q+15 (code q in the low bits), 0 for indices below 0 and
+// outside [0, len) when the whole group is
+__device__ __forceinline__ uint32_t codes16z(const uint32_t* __restrict__ w, int64_t pos, int dir,
+                                             int len, int q) {
+    if (q >= 0) return stream_codes16(w, pos, dir, len, q);
+    if (q <= -16) return 0u;
+    return stream_codes16(w, pos, dir, len, 0) << (2u * uint32_t(-q));
+}
+
+// a' codes of the lane's 32 rows (row r needs a' index base + g*32 + r - 1)
+__device__ __forceinline__ void load_a_planes(const KernelArgs& ka, S16& u, int gl) {
+    const int q = u.base + gl * 32 - 1;
+    uint32_t p0, p1, h0, h1;
+    planes16(codes16z(ka.wa, u.apos, u.dir, u.m, q), p0, p1);
+    planes16(codes16z(ka.wa, u.apos, u.dir, u.m, q + 16), h0, h1);
+    u.a0 = p0 | (h0 << 16);
+    u.a1 = p1 | (h1 << 16);
+}
+
+// b' codes of the lane's rows as of anti-diagonal e: row r needs b' index
+// e - (base + g*32 + r) - 1, decreasing with r
+__device__ __forceinline__ void load_b_planes(const KernelArgs& ka, S16& u, int gl, int e) {
+    const int top = e - (u.base + gl * 32) - 1;  // index of row 0
+    uint32_t p0, p1, h0, h1;
+    // rows 0..15: indices top-15 .. top (row 15 .. row 0)
+    planes16(rev16(codes16z(ka.wb, u.bpos, u.dir, u.n, top - 15)), p0, p1);
+    planes16(rev16(codes16z(ka.wb, u.bpos, u.dir, u.n, top - 31)), h0, h1);
+    u.b0 = p0 | (h0 << 16);
+    u.b1 = p1 | (h1 << 16);
+}
+
+// 0xffff in each 16-bit half whose bit 15 is set, else 0: a byte permute in
+// its sign-replicating form (a selector nibble with its top bit set copies
+// the sign of the selected byte; the __byte_perm intrinsic uses only the
+// low three bits of each nibble, so this is written in PTX)
+__device__ __forceinline__ uint32_t sign_mask16(uint32_t x) {
+    uint32_t r;
+    asm("prmt.b32 %0, %1, 0, 0xBB99;" : "=r"(r) : "r"(x));
+    return r;
+}
+
+template <int G>
+__device__ __forceinline__ uint32_t unit_max_u32(uint32_t v) {
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o, G));
+    return v;
+}
+
+template <int G>
+__device__ __forceinline__ uint32_t unit_max_u16x2(uint32_t v) {
+#pragma unroll
+    for (int o = G / 2; o >= 1; o >>= 1) v = __vimax3_u16x2(v, __shfl_xor_sync(FULL, v, o, G), 0u);
+    return v;
+}
+
+// b' stream codes q..q+15 (code q in the low bits; 0 when q is outside [0, n))
+__device__ __forceinline__ uint32_t b_codes16_of(const KernelArgs& ka, const S16& u, int q) {
+    return stream_codes16(ka.wb, u.bpos, u.dir, u.n, q);
+}
+
+// live key of window row r with relative score u (u >= 0)
+template <int G>
+__device__ __forceinline__ uint32_t live_key(int u, int r) {
+    return LIVE + uint32_t(u) * uint32_t(P16<G>::W) + uint32_t(P16<G>::W - 1 - r);
+}
+
+template <int G>
+__device__ __forceinline__ void unit_init16(const KernelArgs& ka, S16& u, uint32_t id, int gl,
+                                            uint32_t (&Q2)[16], uint32_t (&Q1)[16]) {
+    const Item it = ka.items[id];
+    u.item = id;
+    u.apos = it.a_pos;
+    u.bpos = it.b_pos;
+    u.dir = (it.flags & ITEM_LEFT) ? -1 : 1;
+    u.m = int(it.m);
+    u.n = int(it.n);
+    u.X = it.X;
+    const int32_t slot = ka.mig_slot[id];
+    const int32_t* rec = slot >= 0 ? mig_record(ka, slot) : nullptr;
+    if (rec && rec[MIG_KIND] == MIG_RELATIVE) {
+        // resume a band saved by a narrower level
+        const int rows = rec[MIG_ROWS];
+        u.d = rec[MIG_D];
+        u.base = rec[MIG_BASE];
+        u.lo = rec[MIG_LO];
+        u.hi = rec[MIG_HI];
+        u.best = rec[MIG_BEST];
+        u.T = rec[MIG_T];
+        u.T1 = rec[MIG_T1];
+        u.T2 = rec[MIG_T2];
+        u.bi = rec[MIG_BI];
+        u.bj = rec[MIG_BJ];
+        u.cells = (unsigned long long)uint32_t(rec[MIG_CELLS_LO]) |
+                  ((unsigned long long)uint32_t(rec[MIG_CELLS_HI]) << 32);
+        u.cells0 = u.cells;
+#pragma unroll
+        for (int h = 0; h < 16; ++h) {
+            uint32_t q1 = 0u, q2 = 0u;
+#pragma unroll
+            for (int half = 0; half < 2; ++half) {
+                const int r = gl * 32 + h + 16 * half;
+                const int v1 = r < rows ? rec[kMigHeader + r] : NEGU;
+                const int v2 = r < rows ? rec[kMigHeader + rows + r] : NEGU;
+                q1 |= (v1 >= 0 ? live_key<G>(v1, r) : 0x4000u) << (16 * half);
+                q2 |= (v2 >= 0 ? live_key<G>(v2, r) : 0x4000u) << (16 * half);
+            }
+            Q1[h] = q1;
+            Q2[h] = q2;
+        }
+        load_a_planes(ka, u, gl);
+        load_b_planes(ka, u, gl, u.d - 1);  // the shift register holds anti-diagonal d-1
+        u.q0 = -(1 << 30);                  // forces a prefetch refill at the loop top
+        u.bpre = 0u;
+    } else {
+        u.base = 0;
+        u.lo = 0;
+        u.hi = 0;
+        u.d = 1;
+        u.best = 0;
+        u.T = -it.X;
+        u.T1 = -it.X;
+        u.T2 = -it.X;
+        u.bi = 0;
+        u.bj = 0;
+        u.cells = 0ull;
+        u.cells0 = 0ull;
+        u.q0 = 0;
+        u.bpre = b_codes16_of(ka, u, 16 * gl);
+#pragma unroll
+        for (int h = 0; h < 16; ++h) {
+            Q2[h] = DEAD2;
+            Q1[h] = DEAD2;
+        }
+        // S(0,0) = 0 relative to T_0 = -X, window row 0
+        if (gl == 0) Q1[0] = (DEAD2 & 0xffff0000u) | live_key<G>(it.X, 0);
+        load_a_planes(ka, u, gl);
+        u.b0 = 0u;
+        u.b1 = 0u;
+    }
+    const bool too_big = it.X > kGroupMaxX;  // never binned here; kept for safety
+    u.active = !too_big;
+    u.done = too_big;
+    u.overflow = too_big;
+    u.migrated = false;
+}
+
+// Result or escalation of a finished unit (its leader lane writes).
+__device__ __forceinline__ void unit_finish16(const KernelArgs& ka, const S16& u, int level,
+                                              int gl) {
+    if (gl != 0) return;
+    if (u.overflow) {
+        if (u.migrated) atomicAdd(&ka.counters->cells[level], u.cells - u.cells0);
+        const int nq = escalate_queue(ka, level, false);
+        const unsigned int t = atomicAdd(&ka.counters->tail[nq], 1u);
+        ka.queues[size_t(nq) * ka.qcap + t] = u.item;
+    } else {
+        ExtRes r;
+        r.best = u.best;
+        r.bi = u.bi;
+        r.bj = u.bj;
+        r.status = 0;
+        r.cells = u.cells;
+        ka.ext[u.item] = r;
+        atomicAdd(&ka.counters->cells[level], u.cells - u.cells0);
+    }
+}
+
+// Loop top: slide windows (by half-lanes of 16 rows) so that the next three
+// steps fit, save overflowing bands for the next level, and keep the b'
+// prefetch covering the next three steps.  Q2 = d-2, Q1 = d-1.
+template <int G>
+__device__ __forceinline__ void unit_prepare16(const KernelArgs& ka, S16& u, int level, int gl,
+                                               int unit, uint32_t (&Q2)[16], uint32_t (&Q1)[16]) {
+    constexpr int W = P16<G>::W;
+    const int rlo = max(u.lo, u.d - u.n);
+    const int top = min(u.hi + 3, u.m);  // highest row the next three steps can reach
+    const bool need = u.active && top >= u.base + W;
+    if (__any_sync(FULL, need)) {
+        // keep row rlo - 1 (a predecessor of the lowest cell) in the window
+        const int s = need ? (rlo - 1 - u.base) / 16 : 0;
+        const bool ovf = need && (s <= 0 || top >= u.base + s * 16 + W);
+        const int sh = (need && !ovf) ? s : 0;  // half-lanes to drop
+        const int t = sh >> 1;
+        const bool odd = (sh & 1) != 0;
+        // halves of this lane that receive a row of the old window
+        const bool lo_ok = 2 * gl + sh < 2 * G;
+        const bool hi_ok = 2 * gl + sh + 1 < 2 * G;
+        const uint32_t keep = (lo_ok ? 0x0000ffffu : 0u) | (hi_ok ? 0xffff0000u : 0u);
+        const uint32_t rebase = uint32_t(16 * sh) * 0x10001u;  // row codes grow by 16*sh
+#pragma unroll
+        for (int h = 0; h < 16; ++h) {
+            uint32_t x2 = __shfl_down_sync(FULL, Q2[h], t, G);
+            uint32_t x1 = __shfl_down_sync(FULL, Q1[h], t, G);
+            const uint32_t y2 = __shfl_down_sync(FULL, Q2[h], t + 1, G);
+            const uint32_t y1 = __shfl_down_sync(FULL, Q1[h], t + 1, G);
+            if (odd) {
+                x2 = __byte_perm(x2, y2, 0x5432);
+                x1 = __byte_perm(x1, y1, 0x5432);
+            }
+            if (sh > 0) {
+                Q2[h] = ((x2 + rebase) & keep) | (DEAD2 & ~keep);
+                Q1[h] = ((x1 + rebase) & keep) | (DEAD2 & ~keep);
+            }
+        }
+        {
+            uint32_t xa0 = __shfl_down_sync(FULL, u.a0, t, G), ya0 = __shfl_down_sync(FULL, u.a0, t + 1, G);
+            uint32_t xa1 = __shfl_down_sync(FULL, u.a1, t, G), ya1 = __shfl_down_sync(FULL, u.a1, t + 1, G);
+            uint32_t xb0 = __shfl_down_sync(FULL, u.b0, t, G), yb0 = __shfl_down_sync(FULL, u.b0, t + 1, G);
+            uint32_t xb1 = __shfl_down_sync(FULL, u.b1, t, G), yb1 = __shfl_down_sync(FULL, u.b1, t + 1, G);
+            if (odd) {
+                xa0 = __funnelshift_r(xa0, ya0, 16);
+                xa1 = __funnelshift_r(xa1, ya1, 16);
+                xb0 = __funnelshift_r(xb0, yb0, 16);
+                xb1 = __funnelshift_r(xb1, yb1, 16);
+            }
+            if (sh > 0) {
+                u.a0 = xa0;
+                u.a1 = xa1;
+                u.b0 = xb0;
+                u.b1 = xb1;
+                u.base += 16 * sh;
+                if (!(lo_ok && hi_ok)) {
+                    // rows new to the window: codes from memory (b' as of d-1)
+                    load_a_planes(ka, u, gl);
+                    load_b_planes(ka, u, gl, u.d - 1);
+                }
+            }
+        }
+        if (__any_sync(FULL, ovf)) {
+            // save the band (window rows [base, base + W) of d-1 and d-2, as
+            // 32-bit relative scores) for the next level
+            int32_t slot = -1;
+            if (ovf && gl == 0) slot = mig_alloc(ka, level);
+            slot = __shfl_sync(FULL, slot, unit * G);
+            if (ovf && slot >= 0) {
+                int32_t* rec = mig_record(ka, slot);
+#pragma unroll
+                for (int h = 0; h < 16; ++h) {
+#pragma unroll
+                    for (int half = 0; half < 2; ++half) {
+                        const int r = gl * 32 + h + 16 * half;
+                        const uint32_t s1 = (Q1[h] >> (16 * half)) & 0xffffu;
+                        const uint32_t s2 = (Q2[h] >> (16 * half)) & 0xffffu;
+                        rec[kMigHeader + r] = s1 >= LIVE ? int((s1 - LIVE) >> P16<G>::LOG2W) : NEGU;
+                        rec[kMigHeader + W + r] = s2 >= LIVE ? int((s2 - LIVE) >> P16<G>::LOG2W) : NEGU;
+                    }
+                }
+                if (gl == 0) {
+                    rec[MIG_KIND] = MIG_RELATIVE;
+                    rec[MIG_ROWS] = W;
+                    rec[MIG_D] = u.d;
+                    rec[MIG_BASE] = u.base;
+                    rec[MIG_LO] = u.lo;
+                    rec[MIG_HI] = u.hi;
+                    rec[MIG_BEST] = u.best;
+                    rec[MIG_T] = u.T;
+                    rec[MIG_T1] = u.T1;
+                    rec[MIG_T2] = u.T2;
+                    rec[MIG_BI] = u.bi;
+                    rec[MIG_BJ] = u.bj;
+                    rec[MIG_CELLS_LO] = int32_t(uint32_t(u.cells));
+                    rec[MIG_CELLS_HI] = int32_t(uint32_t(u.cells >> 32));
+                    rec[MIG_LEVEL] = level;
+                    ka.mig_slot[u.item] = slot;
+                }
+            }
+            if (ovf) {
+                u.active = false;
+                u.done = true;
+                u.overflow = true;
+                u.migrated = slot >= 0;
+            }
+        }
+    }
+    // the next three steps read b' stream indices q .. q+2
+    const int q = u.d - u.base - 1;
+    const bool refill = u.active && (q < u.q0 || q + 2 >= u.q0 + P16<G>::PREFETCH);
+    if (__any_sync(FULL, refill)) {
+        if (refill) {
+            u.q0 = q;
+            u.bpre = b_codes16_of(ka, u, q + 16 * gl);
+        }
+    }
+}
+
+// One anti-diagonal step of every unit of the warp.  Q2 = d-2, Q1 = d-1 on
+// entry; O receives d.  Inactive units compute garbage without effects.
+template <int G>
+__device__ __forceinline__ void step16(const KernelArgs& ka, S16& u, int gl, int unit,
+                                       uint32_t (&Q2)[16], uint32_t (&Q1)[16], uint32_t (&O)[16]) {
+    constexpr int W = P16<G>::W;
+    const int rlo = max(u.lo, u.d - u.n);
+    const int rhi = min(u.hi + 1, u.m);
+    const bool run = u.active && rlo <= rhi;
+    // b' shift register: every row takes the code its lower neighbour row
+    // held on d-1; window row 0 takes stream index d - base - 1
+    const int qq = u.d - u.base - 1 - u.q0;
+    const uint32_t pre = __shfl_sync(FULL, u.bpre, unit * G + ((qq >> 4) & (G - 1)));
+    const uint32_t front = pre >> (uint32_t(qq & 15) * 2u);
+    uint32_t c0 = __shfl_up_sync(FULL, u.b0, 1, G);
+    uint32_t c1 = __shfl_up_sync(FULL, u.b1, 1, G);
+    c0 = gl == 0 ? (front << 31) : c0;
+    c1 = gl == 0 ? ((front >> 1) << 31) : c1;
+    u.b0 = __funnelshift_l(c0, u.b0, 1);
+    u.b1 = __funnelshift_l(c1, u.b1, 1);
+    // row r matches iff both code bits agree: bit r of eq
+    const uint32_t eq = ~((u.a0 ^ u.b0) | (u.a1 ^ u.b1));
+    const uint32_t eqB = eq >> 8;  // rows 8.. and 24.. for registers 8..15
+    // register 0's up / diag: (lane g-1's row 31, own row 15)
+    uint32_t xu = __shfl_up_sync(FULL, Q1[15], 1, G);
+    uint32_t xd = __shfl_up_sync(FULL, Q2[15], 1, G);
+    xu = gl == 0 ? DEAD2 : xu;
+    xd = gl == 0 ? DEAD2 : xd;
+    const uint32_t U0 = __byte_perm(xu, Q1[15], 0x5432);
+    const uint32_t D0 = __byte_perm(xd, Q2[15], 0x5432);
+    // per-step offsets in key units (the re-basing of d-1 and d-2 onto T_d),
+    // both halves at once: v = o1W + max(up - 1, left, diag + SM + sub)
+    const int one = ka.one;
+    const int o1W = (ka.sc.gap + u.T1 - u.T) * W;
+    const uint32_t O1 = uint32_t(o1W) * 0x10001u;
+    const int sm = (ka.sc.mismatch + u.T2 - u.T) * W - 1 - o1W;
+    const uint32_t SM = uint32_t(sm) * 0x10001u;
+    const uint32_t M1 = 0x10001u * one;  // "- M1" = minus one in both halves (IMAD)
+    const int dsw = (ka.sc.match - ka.sc.mismatch) * W;  // divisible by 2^7 for W >= 128
+    // rows of this lane inside [rlo, rhi]: bits [k0, k1) of rb
+    const int i0 = u.base + gl * 32;
+    const int k0 = __viaddmin_s32_relu(rlo, -i0, 32);
+    const int k1 = __viaddmin_s32_relu(rhi, 1 - i0, 32);
+    const uint32_t rb = __funnelshift_lc(~0u, 0u, k1) & ~__funnelshift_lc(~0u, 0u, k0);
+    uint32_t L = 0u;
+    uint32_t lk1 = 0u;
+#pragma unroll
+    for (int h = 0; h < 16; ++h) {
+        const uint32_t sU = h ? Q1[h - 1] : U0;
+        const uint32_t sD = h ? Q2[h - 1] : D0;
+        const uint32_t sUm = sU * uint32_t(one) - M1;
+        const uint32_t t = sD * uint32_t(one) + SM;
+        const uint32_t Mh = (h < 8 ? eq : eqB) & (0x10001u << (h & 7));
+        const uint32_t t2 = Mh * uint32_t(dsw >> (h & 7)) + t;
+        const uint32_t u3 = __vimax3_u16x2(sUm, Q1[h], t2);
+        const uint32_t v = u3 * uint32_t(one) + O1;
+        // row h's range bit -> bit 15, row h+16's -> bit 31
+        const uint32_t x = v & (rb * ka.pw16[h]);
+        const uint32_t mk = sign_mask16(x);  // 0xffff per live half
+        const uint32_t p = (v & mk) | (DEAD2 & ~mk);
+        L |= mk & (0x10001u << h);
+        O[h] = p;
+        if (h & 1) lk1 = __vimax3_u16x2(lk1, O[h - 1], p);
+    }
+    // the unit's largest key and its first / last live rows
+    const uint32_t lkey = max(lk1 & 0xffffu, lk1 >> 16);
+    const int fr = __ffs(L) - 1, lr = 31 - __clz(L);
+    const uint32_t flw = L ? (uint32_t(W - (gl * 32 + fr)) | (uint32_t(gl * 32 + lr + 1) << 16)) : 0u;
+    const uint32_t wkey = unit_max_u32<G>(lkey);
+    const uint32_t fl = unit_max_u16x2<G>(flw);
+    if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
+    const bool uv = fl != 0u;
+    if (run && uv) {
+        const int umax = int((wkey - LIVE) >> P16<G>::LOG2W);
+        if (umax > u.X) {  // S > best  <=>  S - T_d > X
+            const int r = W - 1 - int(wkey & uint32_t(W - 1));
+            u.best = u.T + umax;
+            u.bi = u.base + r;
+            u.bj = u.d - u.bi;
+        }
+        u.T2 = u.T1;
+        u.T1 = u.T;
+        u.T = u.best - u.X;
+        u.lo = u.base + (W - int(fl & 0xffffu));
+        u.hi = u.base + int(fl >> 16) - 1;
+    } else if (u.active) {
+        u.active = false;
+        u.done = true;
+    }
+    u.d += 1;
+}
+
+template <int G>
+__global__ void __launch_bounds__(128, 4) k_group16(KernelArgs ka, int level, int queue, int phase) {
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G, unit = lane / G;
+    const uint32_t* q = ka.queues + size_t(queue) * ka.qcap;
+    uint32_t P0[16], P1[16], P2[16];
+#pragma unroll
+    for (int h = 0; h < 16; ++h) {
+        P0[h] = DEAD2;
+        P1[h] = DEAD2;
+        P2[h] = DEAD2;
+    }
+    S16 u;
+    u.active = false;
+    u.done = false;
+    u.overflow = false;
+    u.item = 0;
+    u.m = u.n = 0;
+    u.base = u.lo = u.hi = 0;
+    u.d = 1;
+    u.T = u.T1 = u.T2 = u.best = u.bi = u.bj = 0;
+    u.X = 0;
+    u.cells = 0ull;
+    u.cells0 = 0ull;
+    u.migrated = false;
+    u.apos = u.bpos = 0;
+    u.dir = 1;
+    u.q0 = 0;
+    u.bpre = 0u;
+    u.a0 = u.a1 = u.b0 = u.b1 = 0u;
+    bool exhausted = false;
+    for (;;) {
+        if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
+            if (u.done) {
+                unit_finish16(ka, u, level, gl);
+                u.done = false;
+            }
+            const bool need = !u.active && !exhausted;  // the same in all lanes of a unit
+            uint32_t id = 0xffffffffu;
+            // one pop per warp for all of its idle units
+            const uint32_t want = __ballot_sync(FULL, need && gl == 0);
+            if (want) {
+                const int leader = __ffs(want) - 1;
+                unsigned int first = 0u, limit = 0u;
+                if (lane == leader)
+                    first = pop_slots(ka.counters, queue, phase, unsigned(__popc(want)), &limit);
+                first = __shfl_sync(FULL, first, leader);
+                limit = __shfl_sync(FULL, limit, leader);
+                const unsigned int slot = first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
+                if (need && slot < limit) id = q[slot];
+            }
+            if (need) {
+                if (id != 0xffffffffu) unit_init16<G>(ka, u, id, gl, P0, P1);
+                else exhausted = true;
+            }
+        }
+        if (!__any_sync(FULL, u.active)) break;
+        unit_prepare16<G>(ka, u, level, gl, unit, P0, P1);
+        step16<G>(ka, u, gl, unit, P0, P1, P2);
+        step16<G>(ka, u, gl, unit, P1, P2, P0);
+        step16<G>(ka, u, gl, unit, P2, P0, P1);
+    }
+}
+
+}  // namespace
+
+// level -> G of its packed form (32 rows per lane)
+#define LOGAN_PACKED_LEVELS(X) X(2, 4)
+
+bool packed_level(int level) {
+    switch (level) {
+#define CASE(L, G) case L: return true;
+        LOGAN_PACKED_LEVELS(CASE)
+#undef CASE
+        default: return false;
+    }
+}
+
+cudaError_t launch_packed_level_persistent(int level, const KernelArgs& ka, int grid, int phase,
+                                           cudaStream_t s) {
+    switch (level) {
+#define CASE(L, G)                                                                   \
+    case L:                                                                          \
+        static_assert(P16<G>::W == level_window(L), "a packed form keeps its level's window"); \
+        k_group16<G><<<grid, 128, 0, s>>>(ka, level, level, phase);                  \
+        break;
+        LOGAN_PACKED_LEVELS(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int packed_level_blocks_per_sm(int level) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (level) {
+#define CASE(L, G) \
+    case L: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_group16<G>, 128, 0); break;
+        LOGAN_PACKED_LEVELS(CASE)
+#undef CASE
+        default: break;
+    }
+    return e == cudaSuccess ? n : 0;
+}
+
+}  // namespace logan

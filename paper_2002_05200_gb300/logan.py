@@ -21,7 +21,7 @@ OK = 0
 EINVAL, ENOMEM, EAGAIN, ECUDA, ETIMEOUT, ECANCELED, ERANGE, ENOTFOUND = \
     -22, -12, -11, -5, -110, -125, -34, -2
 OPT_GRAPHS, OPT_TIMING, OPT_FORCE_LEVEL, OPT_MAX_LEVEL, OPT_RING_CAP, OPT_PLAIN_LEVEL = 1, 2, 3, 4, 5, 6
-OPT_DEVICE, OPT_MIGRATION_MB, OPT_CONCURRENT, OPT_LONG_ITEM = 7, 8, 9, 10
+OPT_DEVICE, OPT_MIGRATION_MB, OPT_CONCURRENT, OPT_LONG_ITEM, OPT_PACKED16 = 7, 8, 9, 10, 11
 X_CLASSES = 8
 
 RESULT_DTYPE = np.dtype([("score", "<i4"), ("left", "<i4"), ("right", "<i4"), ("status", "<i4"),
@@ -38,6 +38,7 @@ EXPORTED = ["logan_version", "logan_strerror", "logan_ctx_create", "logan_ctx_de
             "logan_last_stats", "logan_call_stats", "logan_set_level_table",
             "logan_get_level_table", "logan_intpeak", "logan_autotune", "logan_autotune_save",
             "logan_extend_batch_noalloc", "logan_set_escalation", "logan_get_escalation",
+            "logan_matrix_workspace_size", "logan_extend_batch_matrix",
             "logan_server_create", "logan_server_submit",
             "logan_server_poll", "logan_server_wait", "logan_server_cancel", "logan_server_stats",
             "logan_server_destroy"]
@@ -55,7 +56,8 @@ MAX_LEVELS = 8
 class StatsT(ctypes.Structure):
     _fields_ = [("level_ms", ctypes.c_float * (MAX_LEVELS + 1)), ("total_ms", ctypes.c_float),
                 ("items", ctypes.c_uint32 * (MAX_LEVELS + 1)),
-                ("cells", ctypes.c_uint64 * (MAX_LEVELS + 1)), ("launches", ctypes.c_uint32)]
+                ("cells", ctypes.c_uint64 * (MAX_LEVELS + 1)), ("launches", ctypes.c_uint32),
+                ("packed_levels", ctypes.c_uint32)]
 
 
 class TracebackStatsT(ctypes.Structure):
@@ -111,6 +113,11 @@ def lib():
         L.logan_extend_batch.argtypes = ext_args
         L.logan_extend_batch_plain.argtypes = ext_args
         L.logan_extend_batch_affine.argtypes = ext_args[:7] + [ctypes.c_int32] + ext_args[7:]
+        L.logan_matrix_workspace_size.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT),
+                                                  u32, ctypes.POINTER(ctypes.c_size_t)]
+        L.logan_extend_batch_matrix.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.POINTER(SeqsT), p,
+                                                u32, p, ctypes.c_int, i32, i32, i32, p, p,
+                                                ctypes.c_size_t, p, p]
         u64 = ctypes.c_uint64
         L.logan_overlap_candidates.argtypes = [p, ctypes.POINTER(SeqsT), ctypes.c_int, u32, u32, u32,
                                                p, u64, ctypes.POINTER(u64), p]
@@ -356,6 +363,36 @@ class Context:
         _check(rc, "logan_extend_batch_affine")
         return out[:n]
 
+    def extend_matrix(self, A: DevicePool, B: DevicePool, seeds, matrix, gap_open: int = -10,
+                      gap_extend: int = -1, X: int = 50, X_per_pair=None, workspace=None,
+                      out=None, stream=None):
+        """Runs logan_extend_batch_matrix: pools of letter codes (one byte
+        each, < K), the K x K matrix (host array), affine gaps; returns the
+        int32 [n, 10] result tensor."""
+        import torch
+        M = np.ascontiguousarray(matrix, dtype=np.int32)
+        K = int(M.shape[0])
+        n = int(seeds.shape[0])
+        if out is None:
+            out = torch.empty((max(n, 1), 10), dtype=torch.int32, device=f"cuda:{self.device}")
+        ca, cb = A.c(), B.c()
+        if workspace is None:
+            nb = ctypes.c_size_t()
+            _check(lib().logan_matrix_workspace_size(self._h, ctypes.byref(ca), ctypes.byref(cb), n,
+                                                     ctypes.byref(nb)),
+                   "logan_matrix_workspace_size")
+            workspace = torch.empty(max(1, nb.value), dtype=torch.uint8,
+                                    device=f"cuda:{self.device}")
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
+        rc = lib().logan_extend_batch_matrix(
+            self._h, ctypes.byref(ca), ctypes.byref(cb), seeds.data_ptr() if n else None, n,
+            M.ctypes.data, K, gap_open, gap_extend, X,
+            X_per_pair.data_ptr() if X_per_pair is not None else None, workspace.data_ptr(),
+            workspace.numel(), out.data_ptr(), ctypes.c_void_p(stream.cuda_stream))
+        _check(rc, "logan_extend_batch_matrix")
+        return out[:n]
+
     def traceback(self, A: DevicePool, B: DevicePool, seeds, match: int = 1, mismatch: int = -1,
                   gap: int = -1, X: int = 50, X_per_pair=None, stream=None):
         """Alignment paths (logan_traceback_batch): (codes int32 [total],
@@ -488,7 +525,8 @@ class Context:
         _check(lib().logan_call_stats(self._h, back, ctypes.byref(st)), "logan_call_stats")
         n = num_levels() + 1
         return dict(level_ms=list(st.level_ms)[:n], total_ms=st.total_ms,
-                    items=list(st.items)[:n], cells=list(st.cells)[:n], launches=st.launches)
+                    items=list(st.items)[:n], cells=list(st.cells)[:n], launches=st.launches,
+                    packed_levels=st.packed_levels)
 
 
 def batch_to_device(b, packed2bit: Optional[bool] = None, device="cuda"):

@@ -9,7 +9,7 @@ timing reduction use torch.distributed.
 * ``lpt_partition``: longest-processing-time assignment of pairs to ranks by
   estimated work (sum of the two sequence lengths).
 * ``shard_indices``: this rank's pair indices (sorted, so each shard keeps
-  input order).
+  input order); ``shard_batch``: the batch restricted to them.
 * ``gather_results``: reassembles per-rank result arrays in input order on
   every rank.
 * ``reduce_step``: max of the step time and sum of the cells over ranks.
@@ -45,6 +45,15 @@ def lpt_partition(work: np.ndarray, world: int):
 
 def shard_indices(b, world: int, rank: int) -> np.ndarray:
     return lpt_partition(pair_work(b), world)[rank]
+
+
+def shard_batch(b, idx: np.ndarray):
+    """This rank's pairs as a batch of its own: the same sequence pools (each
+    rank holds the whole read set), the seeds and per-pair X of `idx` only."""
+    import dataclasses
+    return dataclasses.replace(b, seeds=b.seeds[idx].copy(),
+                               Xs=None if b.Xs is None else b.Xs[idx].copy(),
+                               name=f"{b.name}[shard]")
 
 
 def gather_results(local: np.ndarray, idx: np.ndarray, n_total: int, group=None) -> np.ndarray:

@@ -458,6 +458,69 @@ def serving_requests(n_requests: int, rate: float, seed: int = 4,
     return out
 
 
+class PairLibrary:
+    """A library of seeded pairs from which serving requests are drawn.
+
+    Every sequence is stored 2-bit packed from a 16-base boundary, so a
+    request's pools are plain concatenations of word ranges and cost one
+    vectorised gather to build.  Pairs are independent, so a pair's result
+    is the same in every request that draws it.
+    """
+
+    def __init__(self, b: "Batch"):
+        assert not b.packed and not b.shared_pool
+        self.n_pairs = b.n_pairs
+        self.X = b.X
+        self.seeds = b.seeds.copy()
+        self.sides = []
+        for pool, off, ln, col in ((b.poolA, b.offA, b.lenA, "idxA"),
+                                   (b.poolB, b.offB, b.lenB, "idxB")):
+            ln = ln[b.seeds[col]].astype(np.uint32)          # one sequence per pair
+            src = off[b.seeds[col]].astype(np.int64)
+            nw = (ln.astype(np.int64) + 15) // 16            # whole words per sequence
+            wo = np.concatenate([[0], np.cumsum(nw)[:-1]]).astype(np.int64)
+            asc = np.full(int(nw.sum()) * 16, ord("A"), dtype=np.uint8)
+            for i in range(ln.size):
+                asc[wo[i] * 16:wo[i] * 16 + int(ln[i])] = pool[src[i]:src[i] + int(ln[i])]
+            self.sides.append((pack2bit(asc), wo, nw, ln))
+        self.meta = dict(b.meta)
+
+    @property
+    def total_bases(self) -> int:
+        return int(sum(int(s[3].sum(dtype=np.uint64)) for s in self.sides))
+
+    def request(self, idx, name: str = "request") -> "Batch":
+        """A packed batch holding library pairs `idx` (in that order)."""
+        idx = np.asarray(idx, dtype=np.int64)
+        parts = []
+        for words, wo, nw, ln in self.sides:
+            cnt = nw[idx]
+            start = np.concatenate([[0], np.cumsum(cnt)[:-1]]).astype(np.int64)
+            a, c = wo[idx].tolist(), cnt.tolist()
+            w = np.concatenate([words[x:x + n] for x, n in zip(a, c)] +
+                               [np.zeros(1, np.uint32)])
+            parts.append((w, (start * 16).astype(np.uint64), ln[idx].copy()))
+        sd = np.zeros(idx.size, dtype=SEED_DTYPE)
+        sd["idxA"] = sd["idxB"] = np.arange(idx.size, dtype=np.uint32)
+        for f in ("posA", "posB", "len"):
+            sd[f] = self.seeds[f][idx]
+        (wa, oa, la), (wb, ob, lb) = parts
+        return Batch(name, wa, oa, la, wb, ob, lb, sd, self.X, packed=True,
+                     meta=dict(library_pairs=idx))
+
+
+def serving_library(n_pairs: int = 30_000, seed: int = 5, X: int = 50,
+                    max_len: Optional[int] = None) -> PairLibrary:
+    """Pairs drawn like the uneven-length mixture (1 kbp - 1 Mbp, error
+    U[5, 20] %), one X for all, as a PairLibrary."""
+    return PairLibrary(uneven_batch(n_pairs, seed=seed, max_len=max_len, X_choices=(X,)))
+
+
+def request_sizes(rng: np.random.Generator, n: int, max_pairs: int = 10_000) -> np.ndarray:
+    """Request sizes round(exp(U[0, ln max_pairs])), at least 1 (log-uniform)."""
+    return np.maximum(np.rint(np.exp(rng.uniform(0, np.log(max_pairs), size=n))), 1).astype(int)
+
+
 def tiny_pairs(n_pairs: int, max_len: int, seed: int, alphabet: bytes = b"ACGT",
                X_choices=(0, 1, 2, 5, 10, 50)) -> Batch:
     """Random short pairs with arbitrary (in-bounds) seeds, for edge-case tests:
@@ -477,6 +540,104 @@ def tiny_pairs(n_pairs: int, max_len: int, seed: int, alphabet: bytes = b"ACGT",
     Xs = np.asarray(X_choices, dtype=np.int32)[rng.integers(0, len(X_choices), size=n_pairs)]
     return Batch("tiny_pairs", poolA, _offsets(lenA), lenA, poolB, _offsets(lenB), lenB,
                  seeds, int(max(X_choices)), Xs=Xs, meta=dict(seed=seed, max_len=max_len))
+
+
+# ---------------------------------------------------------------------------
+# protein pairs (substitution-matrix scoring)
+
+# BLOSUM62 over the 20 standard amino acids, in this letter order (letter
+# code = index), typed from the published table (Henikoff & Henikoff 1992).
+AMINO = "ARNDCQEGHILKMFPSTWYV"
+BLOSUM62 = np.array([
+    [4, -1, -2, -2, 0, -1, -1, 0, -2, -1, -1, -1, -1, -2, -1, 1, 0, -3, -2, 0],
+    [-1, 5, 0, -2, -3, 1, 0, -2, 0, -3, -2, 2, -1, -3, -2, -1, -1, -3, -2, -3],
+    [-2, 0, 6, 1, -3, 0, 0, 0, 1, -3, -3, 0, -2, -3, -2, 1, 0, -4, -2, -3],
+    [-2, -2, 1, 6, -3, 0, 2, -1, -1, -3, -4, -1, -3, -3, -1, 0, -1, -4, -3, -3],
+    [0, -3, -3, -3, 9, -3, -4, -3, -3, -1, -1, -3, -1, -2, -3, -1, -1, -2, -2, -1],
+    [-1, 1, 0, 0, -3, 5, 2, -2, 0, -3, -2, 1, 0, -3, -1, 0, -1, -2, -1, -2],
+    [-1, 0, 0, 2, -4, 2, 5, -2, 0, -3, -3, 1, -2, -3, -1, 0, -1, -3, -2, -2],
+    [0, -2, 0, -1, -3, -2, -2, 6, -2, -4, -4, -2, -3, -3, -2, 0, -2, -2, -3, -3],
+    [-2, 0, 1, -1, -3, 0, 0, -2, 8, -3, -3, -1, -2, -1, -2, -1, -2, -2, 2, -3],
+    [-1, -3, -3, -3, -1, -3, -3, -4, -3, 4, 2, -3, 1, 0, -3, -2, -1, -3, -1, 3],
+    [-1, -2, -3, -4, -1, -2, -3, -4, -3, 2, 4, -2, 2, 0, -3, -2, -1, -2, -1, 1],
+    [-1, 2, 0, -1, -3, 1, 1, -2, -1, -3, -2, 5, -1, -3, -1, 0, -1, -3, -2, -2],
+    [-1, -1, -2, -3, -1, 0, -2, -3, -2, 1, 2, -1, 5, 0, -2, -1, -1, -1, -1, 1],
+    [-2, -3, -3, -3, -2, -3, -3, -3, -1, 0, 0, -3, 0, 6, -4, -2, -2, 1, 3, -1],
+    [-1, -2, -2, -1, -3, -1, -1, -2, -2, -3, -3, -1, -2, -4, 7, -1, -1, -4, -3, -2],
+    [1, -1, 1, 0, -1, 0, 0, 0, -1, -2, -2, 0, -1, -2, -1, 4, 1, -3, -2, -2],
+    [0, -1, 0, -1, -1, -1, -1, -2, -2, -1, -1, -1, -1, -2, -1, 1, 5, -2, -2, 0],
+    [-3, -3, -4, -4, -2, -2, -3, -2, -2, -3, -2, -3, -1, 1, -4, -3, -2, 11, 2, -3],
+    [-2, -2, -2, -3, -2, -1, -2, -3, 2, -1, -1, -2, -1, 3, -3, -2, -2, 2, 7, -1],
+    [0, -3, -3, -3, -1, -2, -2, -3, -3, 3, 1, -2, 1, -1, -2, -2, 0, -3, -1, 4],
+], dtype=np.int32)
+
+
+def dna_matrix(match: int = 1, mismatch: int = -1) -> np.ndarray:
+    """The 4 x 4 match / mismatch matrix over the codes A0 C1 G2 T3."""
+    M = np.full((4, 4), mismatch, dtype=np.int32)
+    np.fill_diagonal(M, match)
+    return M
+
+
+def protein_pairs(n_pairs: int = 20_000, lo: int = 100, hi: int = 2_000, err: float = 0.25,
+                  related_frac: float = 0.8, seed_len: int = 8, X: int = 60,
+                  seed: int = 12) -> Batch:
+    """Seeded protein pairs as letter codes 0..19 (AMINO order), one byte each.
+
+    A: uniform letters, length log-uniform in [lo, hi].  Related pairs: B is
+    A with an edit at each position with probability err (substitution by a
+    uniform other letter, insertion of a uniform letter, deletion: equally
+    likely), the seed_len letters at A's midpoint protected and mapped into
+    B.  Unrelated pairs: an independent B of its own length, A's seed
+    k-mer written at a uniform position of B.  Pools hold codes, not ASCII."""
+    rng = np.random.default_rng([seed, 7])
+    n_rel = int(round(related_frac * n_pairs))
+    lenA = np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi), size=n_pairs))).astype(np.int64)
+    lenA = np.maximum(lenA, seed_len)
+    posA = (lenA - seed_len) // 2
+    As, Bs, posB = [], [], np.zeros(n_pairs, np.int64)
+    for p in range(n_pairs):
+        a = rng.integers(0, 20, size=int(lenA[p])).astype(np.uint8)
+        if p < n_rel:
+            out, pb = [], 0
+            for t in range(a.size):
+                if posA[p] <= t < posA[p] + seed_len:
+                    if t == posA[p]:
+                        pb = len(out)
+                    out.append(a[t])
+                    continue
+                if rng.random() < err:
+                    kind = rng.integers(0, 3)
+                    if kind == 0:
+                        out.append(np.uint8((a[t] + rng.integers(1, 20)) % 20))
+                    elif kind == 1:
+                        out.append(np.uint8(rng.integers(0, 20)))
+                        out.append(a[t])
+                    continue  # deletion (kind 2) keeps nothing
+                out.append(a[t])
+            b = np.array(out, dtype=np.uint8)
+        else:
+            lb = int(np.rint(np.exp(rng.uniform(np.log(lo), np.log(hi)))))
+            lb = max(lb, seed_len)
+            b = rng.integers(0, 20, size=lb).astype(np.uint8)
+            pb = int(rng.integers(0, lb - seed_len + 1))
+            b[pb:pb + seed_len] = a[posA[p]:posA[p] + seed_len]
+        As.append(a)
+        Bs.append(b)
+        posB[p] = pb
+    order = rng.permutation(n_pairs)  # related and unrelated mixed
+    As = [As[i] for i in order]
+    Bs = [Bs[i] for i in order]
+    lA = np.array([x.size for x in As], np.uint32)
+    lB = np.array([x.size for x in Bs], np.uint32)
+    seeds = np.zeros(n_pairs, dtype=SEED_DTYPE)
+    seeds["idxA"] = seeds["idxB"] = np.arange(n_pairs, dtype=np.uint32)
+    seeds["posA"] = posA[order]
+    seeds["posB"] = posB[order]
+    seeds["len"] = seed_len
+    return Batch("protein_pairs", np.concatenate(As), _offsets(lA), lA, np.concatenate(Bs),
+                 _offsets(lB), lB, seeds, X,
+                 meta=dict(n_pairs=n_pairs, seed=seed, alphabet=AMINO, related=order < n_rel))
 
 
 # ---------------------------------------------------------------------------

@@ -23,17 +23,19 @@ def run_oracle(b, threads=None):
     return res
 
 
-def run_oracle_all(b, chunk=8192, threads=None):
+def run_oracle_all(b, chunk=8192, threads=None, run=None):
     """The oracle on every pair of a (possibly 2-bit packed) batch, on all
     host cores: pairs ordered longest first so the long extensions start
     early, in chunks of `chunk` pairs (each chunk's sequences decoded to
-    ASCII on its own, which bounds host memory); results in input order."""
+    ASCII on its own, which bounds host memory); results in input order.
+    `run(sub)` replaces the linear oracle (e.g. the affine one)."""
     key = (b.lenA[b.seeds["idxA"]].astype(np.int64) + b.lenB[b.seeds["idxB"]].astype(np.int64))
     order = np.argsort(-key, kind="stable")
     out = np.zeros(b.n_pairs, dtype=oracle.PAIR_DTYPE)
     for c0 in range(0, b.n_pairs, chunk):
         idx = order[c0:c0 + chunk]
-        out[idx] = run_oracle(b.subset(idx), threads)
+        sub = b.subset(idx)
+        out[idx] = run_oracle(sub, threads) if run is None else run(sub)
     return out
 
 

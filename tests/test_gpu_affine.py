@@ -5,7 +5,7 @@ import pytest
 
 import oracle
 from paper_2002_05200_gb300 import logan, synth
-from tests.gpu_common import assert_same
+from tests.gpu_common import assert_same, run_oracle_all
 
 pytestmark = pytest.mark.gpu
 
@@ -74,31 +74,63 @@ def test_zero_open_equals_linear_path(ctx):
     assert np.array_equal(logan.results_to_numpy(lin), logan.results_to_numpy(aff))
 
 
-def test_wide_bands_report_erange(ctx):
-    # unpruned: a side's widest anti-diagonal has min(m, n) + 1 cells; above
-    # the 512-row window the pair is LOGAN_ERANGE, the rest are exact
+def test_wide_bands_continue_in_the_ring(ctx):
+    # unpruned: a side's widest anti-diagonal has min(m, n) + 1 cells; bands
+    # above the 512-row register window continue in the device-memory ring
+    # and every pair is exact
     b = synth.tiny_pairs(60, 1500, seed=8, X_choices=(200_000,))
     g = run_affine(ctx, b, -2, -1)
-    ref = ref_affine(b, -2, -1)
     s = b.seeds
     lA, lB = b.lenA[s["idxA"]].astype(np.int64), b.lenB[s["idxB"]].astype(np.int64)
     left = np.minimum(s["posA"], s["posB"]).astype(np.int64) + 1
     right = np.minimum(lA - s["posA"] - s["len"], lB - s["posB"] - s["len"]) + 1
     wide = np.maximum(left, right) > 512
     assert wide.any() and (~wide).any()
-    assert np.all(g["status"][wide] == logan.ERANGE)
-    for f in ("score", "left", "right", "begA", "begB", "endA", "endB", "cells"):
-        assert np.array_equal(g[f][~wide].astype(np.int64), ref[f][~wide].astype(np.int64)), f
+    assert_same(g, ref_affine(b, -2, -1), "bands up to 1500 rows")
 
 
-def test_x_beyond_key_range_reports_erange(ctx):
+def test_x_beyond_key_range_is_exact(ctx):
+    # X too large for the register windows' keys: the ring kernel runs them
     b = synth.uniform_pairs(n_pairs=20)
     b.Xs = np.full(b.n_pairs, (1 << 20), dtype=np.int32)
     b.Xs[::2] = 50
+    assert_same(run_affine(ctx, b, -2, -1), ref_affine(b, -2, -1), "X = 2^20 and 50")
+
+
+def test_uneven_pairs_x500_no_erange(ctx):
+    # the uneven length mixture (up to 200 kbp here) at X = 500 with affine
+    # gaps: bands beyond 512 rows included, zero LOGAN_ERANGE, every pair
+    # exact
+    b = synth.uneven_batch(n_pairs=120, max_len=200_000, seed=31, X_choices=(500,))
+    g = run_affine(ctx, b, -2, -1, packed2bit=True)
+    assert np.all(g["status"] == logan.OK)
+    assert_same(g, run_oracle_all(b, run=lambda sub: ref_affine(sub, -2, -1)),
+                "uneven, X = 500")
+
+
+def test_band_beyond_the_ring_reports_erange(ctx):
+    # identical 40 kbp sequences at X = 2^20: the unpruned band outgrows the
+    # ring's 32,768 rows -> LOGAN_ERANGE for that pair, the others exact
+    rng = np.random.default_rng(12)
+    seq = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, 40_000)]
+    base = synth.uniform_pairs(n_pairs=8, length=1200, seed=13)
+    poolA = np.concatenate([seq, base.poolA])
+    poolB = np.concatenate([seq, base.poolB])
+    offA = np.concatenate([[0], base.offA.astype(np.int64) + 40_000]).astype(np.uint64)
+    offB = np.concatenate([[0], base.offB.astype(np.int64) + 40_000]).astype(np.uint64)
+    lenA = np.concatenate([[40_000], base.lenA]).astype(np.uint32)
+    lenB = np.concatenate([[40_000], base.lenB]).astype(np.uint32)
+    seeds = np.zeros(9, dtype=base.seeds.dtype)
+    seeds[0] = (0, 0, 0, 0, 0)
+    seeds[1:] = base.seeds
+    seeds["idxA"][1:] += 1
+    seeds["idxB"][1:] += 1
+    Xs = np.full(9, 50, np.int32)
+    Xs[0] = 1 << 20
+    b = synth.Batch("ring_limit", poolA, offA, lenA, poolB, offB, lenB, seeds, 50, Xs)
     g = run_affine(ctx, b, -2, -1)
-    assert np.all(g["status"][1::2] == logan.ERANGE)
-    ref = ref_affine(b.subset(np.arange(0, b.n_pairs, 2)), -2, -1)
-    assert_same(g[::2], ref, "small X")
+    assert g["status"][0] == logan.ERANGE
+    assert_same(g[1:], ref_affine(b.subset(np.arange(1, 9)), -2, -1), "the other pairs")
 
 
 def test_argument_errors(ctx):
@@ -111,15 +143,15 @@ def test_argument_errors(ctx):
         assert e.value.code == logan.EINVAL
 
 
-def test_lognormal_100k_sampled(ctx):
-    # the affine bench workload at full size, in its launch configuration
+def test_lognormal_100k_every_pair(ctx):
+    # the affine bench workload at full size, in its launch configuration,
+    # every pair against the affine oracle
     b = synth.lognormal_batch()
     g = run_affine(ctx, b, -2, -1, packed2bit=True)
     ok = g["status"] == logan.OK
-    assert np.all(ok | (g["status"] == logan.ERANGE))
-    rng = np.random.default_rng(201)
-    idx = np.unique(rng.choice(b.n_pairs, 300, replace=False))
-    assert_same(g[idx], ref_affine(b.subset(idx), -2, -1), "lognormal 100K sample")
+    assert np.all(ok)
+    assert_same(g, run_oracle_all(b, run=lambda sub: ref_affine(sub, -2, -1)),
+                "lognormal 100K, every pair")
     k = b.seeds["len"].astype(np.int64)
     assert np.array_equal(g["score"][ok].astype(np.int64),
                           (g["left"].astype(np.int64) + k * b.match + g["right"])[ok])

@@ -25,7 +25,8 @@ def _reset(ctx):
     for opt, v in ((logan.OPT_FORCE_LEVEL, -1), (logan.OPT_MAX_LEVEL, logan.num_levels() - 1),
                    (logan.OPT_GRAPHS, 0), (logan.OPT_RING_CAP, 16), (logan.OPT_PLAIN_LEVEL, 1),
                    (logan.OPT_TIMING, 0), (logan.OPT_MIGRATION_MB, 64),
-                   (logan.OPT_CONCURRENT, 1), (logan.OPT_LONG_ITEM, -2)):
+                   (logan.OPT_CONCURRENT, 1), (logan.OPT_LONG_ITEM, -2),
+                   (logan.OPT_PACKED16, 1)):
         ctx.set_option(opt, v)
     yield
 
@@ -282,3 +283,58 @@ def test_long_item_forms(ctx, long_item):
     assert_same(run_gpu(ctx, b, packed2bit=True, graphs=True), ref, f"long item {long_item}, graph")
     with pytest.raises(logan.LoganError):
         ctx.set_option(logan.OPT_LONG_ITEM, -3)
+
+
+def _packed_case(name):
+    """(batch, packed2bit, options) of the packed 16-bit level tests."""
+    if name == "uniform_ascii":
+        return synth.uniform_pairs(n_pairs=400), False, {}
+    if name == "lognormal":  # unrelated pairs outgrow 128 rows: records out of level 2
+        return synth.lognormal_batch(n_pairs=300), True, {}
+    if name == "uneven_per_pair_x":
+        return synth.uneven_batch(n_pairs=200, max_len=60_000), True, {}
+    if name == "tiny":
+        return synth.tiny_pairs(3000, 40, seed=7), False, {}
+    if name == "escalate_into":  # start at 32 rows: records into level 2
+        return synth.uniform_pairs(n_pairs=200, X=70, seed=3), True, {logan.OPT_FORCE_LEVEL: 0}
+    if name == "restart":  # no band-state records: overflowing bands restart
+        return synth.lognormal_batch(n_pairs=200, seed=5), True, {logan.OPT_MIGRATION_MB: 0}
+    if name == "scoring_2_3_5":
+        b = synth.lognormal_batch(n_pairs=200, seed=6, X=60)
+        b.match, b.mismatch, b.gap = 2, -3, -5
+        return b, True, {}
+    raise ValueError(name)
+
+
+@pytest.mark.parametrize("packed16", [0, 1])
+@pytest.mark.parametrize("name", ["uniform_ascii", "lognormal", "uneven_per_pair_x", "tiny",
+                                  "escalate_into", "restart", "scoring_2_3_5"])
+def test_packed16_level(ctx, name, packed16):
+    # the packed 16-bit form of level 2 (two cells per 32-bit register) and
+    # the 32-bit form give the oracle's results; the call reports which ran
+    b, packed, opts = _packed_case(name)
+    ref = run_oracle(b)
+    for k, v in opts.items():
+        ctx.set_option(k, v)
+    ctx.set_option(logan.OPT_PACKED16, packed16)
+    ctx.set_option(logan.OPT_TIMING, 1)
+    # several extensions to a warp at every level (a small batch would
+    # otherwise run in the one-warp forms, which have no packed variant)
+    ctx.set_option(logan.OPT_LONG_ITEM, -1)
+    g = run_gpu(ctx, b, packed2bit=packed)
+    st = ctx.last_stats()
+    assert bool(st["packed_levels"] & (1 << 2)) == bool(packed16), st["packed_levels"]
+    if name not in ("tiny",):
+        assert st["items"][2] > 0  # level 2 did run
+    assert_same(g, ref, f"{name}, packed16={packed16}")
+
+
+def test_packed16_bounds_select_the_32bit_form(ctx):
+    # scores that do not fit 16 bits at level 2's window keep the 32-bit form
+    b = synth.lognormal_batch(n_pairs=60, seed=8, X=100)
+    b.match, b.mismatch, b.gap = 300, -300, -300
+    ref = run_oracle(b)
+    ctx.set_option(logan.OPT_TIMING, 1)
+    g = run_gpu(ctx, b, packed2bit=True)
+    assert ctx.last_stats()["packed_levels"] == 0
+    assert_same(g, ref, "large scores")
