@@ -338,3 +338,23 @@ def test_packed16_bounds_select_the_32bit_form(ctx):
     g = run_gpu(ctx, b, packed2bit=True)
     assert ctx.last_stats()["packed_levels"] == 0
     assert_same(g, ref, "large scores")
+
+
+@pytest.mark.parametrize("packed16", [0, 1])
+@pytest.mark.parametrize("level", [2, 3, 4, 5])
+def test_packed16_every_level(ctx, level, packed16):
+    # every packed level (windows of 128, 256, 512 and 1024 rows) started
+    # directly; narrower bands stay, wider ones escalate to the next level
+    # (band-state records in both directions between packed and 32-bit
+    # levels); scalar X so that the bound holds for the forced level
+    b = synth.lognormal_batch(n_pairs=400, median=6000, lo=1000, hi=20_000, seed=23)
+    ref = run_oracle(b)
+    ctx.set_option(logan.OPT_FORCE_LEVEL, level)
+    ctx.set_option(logan.OPT_PACKED16, packed16)
+    ctx.set_option(logan.OPT_LONG_ITEM, -1)
+    ctx.set_option(logan.OPT_TIMING, 1)
+    g = run_gpu(ctx, b, packed2bit=True)
+    st = ctx.last_stats()
+    assert bool(st["packed_levels"] & (1 << level)) == bool(packed16), st["packed_levels"]
+    assert st["items"][level] > 0
+    assert_same(g, ref, f"level {level}, packed16={packed16}")
