@@ -442,9 +442,9 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
 #define LOGAN_OPT_PACKED16 11    /* 1 (default): a window level that has a
                                     packed form (two 16-bit cells per 32-bit
                                     register) runs it when the call's scoring
-                                    and X provably fit 16 bits -- for a window
-                                    of W rows, W * (Xmax + 2*max(match,0) +
-                                    |gap| + 2) <= 32767 and W * (|mismatch| +
+                                    and X provably fit 16 bits --
+                                    128 * (Xmax + 2*max(match,0) + |gap| + 2)
+                                    + 31 <= 32767 and 128 * (|mismatch| +
                                     |gap| + 2*max(match,0) + 2) <= 16383, Xmax
                                     the largest X that can reach the level
                                     (the scalar X, or the X-class bounds of

@@ -261,9 +261,9 @@ AuxSet* aux_for(logan_ctx* c, cudaStream_t s) {
 }
 
 // Levels that run in their packed 16-bit form in this call: those with a
-// packed kernel whose window W satisfies
-//   W * (Xmax + 2*max(match,0) + |gap| + 2) <= 32767  and
-//   W * (|mismatch| + |gap| + 2*max(match,0) + 2) <= 16383,
+// packed kernel, when
+//   128 * (Xmax + 2*max(match,0) + |gap| + 2) + 31 <= 32767  and
+//   128 * (|mismatch| + |gap| + 2*max(match,0) + 2) <= 16383,
 // Xmax the largest X that can reach the level: the scalar X when there is
 // no per-pair X and no forced start level, else the upper bound of every X
 // class whose start level is at or below it (items only move to wider
@@ -287,8 +287,8 @@ uint32_t packed16_levels(const logan_ctx* c, Scoring sc, int32_t X, const int32_
             for (int k = 0; k < kXClasses; ++k)
                 if (tab.lv[k] <= l) xmax = std::max(xmax, upper[k]);
         }
-        const int64_t W = level_window(l);
-        if (W * (xmax + 2 * mp + ag + 2) <= 32767 && W * (am + ag + 2 * mp + 2) <= 16383)
+        constexpr int64_t S = 128;  // score scale of the packed keys
+        if (S * (xmax + 2 * mp + ag + 2) + 31 <= 32767 && S * (am + ag + 2 * mp + 2) <= 16383)
             mask |= 1u << l;
     }
     return mask;
@@ -414,6 +414,22 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         c->launches_last = launches + 2;
         return LOGAN_OK;
     }
+    // With one X for the whole batch the host knows every item's start queue
+    // (the binning's rule): only those launch in phase 1, and phase 2 starts
+    // above that level (a level only receives items from narrower ones).
+    uint32_t start_units = ~0u;
+    int first_escalated = plain ? first + 1 : 0;
+    if (!plain && !Xs && tab.only_xclass < 0) {
+        const int64_t forced_start = c->force_level >= 0 ? c->force_level : -1;
+        int l = forced_start >= 0 ? int(forced_start) : int(tab.lv[x_class(X)]);
+        if (X > kGroupMaxX && l < kWarpLevels) l = kWarpLevels;
+        l = std::min(l, maxl);
+        start_units = 0u;
+        const bool twin_form = l < kTwinLevels;
+        if (twin_form && tab.long_min != 0xffffffffu) start_units |= 1u << (kNumLevels + l);
+        if (!(twin_form && tab.long_min == 0u)) start_units |= 1u << l;
+        first_escalated = l + 1;
+    }
     uint32_t p1_levels = 0, p2_levels = 0;
     cudaEvent_t* ev = c->ev;
     auto rec = [&](int idx, cudaStream_t st) {
@@ -437,7 +453,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         if (ax && cudaEventRecord(ax->fork, s) != cudaSuccess) return LOGAN_ECUDA;
         for (int k = 0; k < kUnits; ++k) {
             const int u = k < kTwinLevels ? kNumLevels + k : k - kTwinLevels;
-            if (unit_level(u) > maxl) continue;
+            if (unit_level(u) > maxl || !((start_units >> u) & 1u)) continue;
             cudaStream_t st = ax ? ax->st[u] : s;
             if (ax && cudaStreamWaitEvent(st, ax->fork, 0) != cudaSuccess) return LOGAN_ECUDA;
             if (!rec(EV_P1S + u, st)) return LOGAN_ECUDA;
@@ -452,7 +468,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     }
     // phase 2: escalated items, narrowest level first (a queue only receives
     // items from narrower levels); a level's latency form after the level
-    for (int lvl = (plain ? first + 1 : 0); lvl <= maxl; ++lvl) {
+    for (int lvl = first_escalated; lvl <= maxl; ++lvl) {
         for (int u : {lvl, lvl < kTwinLevels && !plain ? kNumLevels + lvl : -1}) {
             if (u < 0) continue;
             if (!rec(EV_P2S + u, s)) return LOGAN_ECUDA;

@@ -13,17 +13,20 @@
 // (both halves move together), and only register 0 needs the neighbour
 // lane's top row (one shuffle and one byte permute per anti-diagonal).
 //
-// Values.  A cell at window row r of anti-diagonal e holds
-//     sigma = 32768 + u*W + (W - 1 - r),   u = S - T_e,  T_e = best_{<e} - X,
+// Values.  The cell in row k of lane g's 32 rows on anti-diagonal e holds
+//     sigma = 32768 + 128*u + (31 - k),   u = S - T_e,  T_e = best_{<e} - X,
 // when it is live (u >= 0, i.e. sigma >= 32768, bit 15 set), and DEAD =
-// 16384 otherwise.  The low log2(W) bits are the row code, so one unsigned
-// 16-bit maximum over a unit gives the anti-diagonal's best score and, for
-// equal scores, its smallest row (the tie-break of the 32-bit kernel's
-// keyed max).  Every candidate is re-based onto the cell's own row code:
-// "up" and "diag" come from row r - 1 (code + 1) and get -1, "left" from the
-// same row.  The host enables this kernel only when
-//     W*(Xmax + 2*max(match,0) + |gap| + 2) <= 32767   and
-//     W*(|mismatch| + |gap| + 2*max(match,0) + 2) <= 16383,
+// 16384 otherwise.  The low bits are the row's code within its lane, so one
+// unsigned 16-bit maximum over a lane gives the lane's best score and, for
+// equal scores, its smallest row; the unit's reduction then widens the key
+// to 32 bits with the lane, (u << log2 W) | (W - 1 - row), so one maximum
+// gives the anti-diagonal's best and its smallest row (the tie-break of the
+// 32-bit kernel's keyed max).  Every candidate is re-based onto the cell's
+// own code: "up" and "diag" come from row k - 1 (code + 1) and get -1, "left"
+// from the same row; row 0's predecessors are the lower lane's row 31 (code
+// 0), which first get +32.  The host enables this kernel only when
+//     128*(Xmax + 2*max(match,0) + |gap| + 2) + 31 <= 32767   and
+//     128*(|mismatch| + |gap| + 2*max(match,0) + 2) <= 16383,
 // Xmax the largest X that can reach the level.  Then every half-word stays
 // inside [0, 65536) through every addition, so the additions are plain
 // 32-bit multiply-adds of both halves at once (FMA pipe, no carry or borrow
@@ -57,13 +60,15 @@ template <int G>
 struct P16 {
     static constexpr int C = 32;  // rows per lane (16 registers per anti-diagonal)
     static constexpr int W = G * C;
-    static constexpr int LOG2W = W == 32 ? 5 : W == 64 ? 6 : W == 128 ? 7 : W == 256 ? 8 : 9;
+    static constexpr int LOG2W =
+        W == 32 ? 5 : W == 64 ? 6 : W == 128 ? 7 : W == 256 ? 8 : W == 512 ? 9 : 10;
     static constexpr int PREFETCH = 16 * G;
     static_assert((1 << LOG2W) == W, "window must be a power of two");
-    // the substitution step multiplies a match flag at bit h' < 8 by
-    // (match - mismatch) * W >> h', exact only for W >= 128
-    static_assert(W >= 128, "packed levels need a window of at least 128 rows");
 };
+// score scale of a key: the substitution step multiplies a match flag at bit
+// h' < 8 by (match - mismatch) * 128 >> h', which is exact
+constexpr int KS = 128;
+constexpr int LOG2KS = 7;
 
 struct S16 {
     int base, lo, hi, d;
@@ -154,10 +159,9 @@ __device__ __forceinline__ uint32_t b_codes16_of(const KernelArgs& ka, const S16
     return stream_codes16(ka.wb, u.bpos, u.dir, u.n, q);
 }
 
-// live key of window row r with relative score u (u >= 0)
-template <int G>
-__device__ __forceinline__ uint32_t live_key(int u, int r) {
-    return LIVE + uint32_t(u) * uint32_t(P16<G>::W) + uint32_t(P16<G>::W - 1 - r);
+// live key of row k of a lane with relative score u (u >= 0)
+__device__ __forceinline__ uint32_t live_key(int u, int k) {
+    return LIVE + uint32_t(u) * uint32_t(KS) + uint32_t(31 - k);
 }
 
 template <int G>
@@ -197,8 +201,8 @@ __device__ __forceinline__ void unit_init16(const KernelArgs& ka, S16& u, uint32
                 const int r = gl * 32 + h + 16 * half;
                 const int v1 = r < rows ? rec[kMigHeader + r] : NEGU;
                 const int v2 = r < rows ? rec[kMigHeader + rows + r] : NEGU;
-                q1 |= (v1 >= 0 ? live_key<G>(v1, r) : 0x4000u) << (16 * half);
-                q2 |= (v2 >= 0 ? live_key<G>(v2, r) : 0x4000u) << (16 * half);
+                q1 |= (v1 >= 0 ? live_key(v1, h + 16 * half) : 0x4000u) << (16 * half);
+                q2 |= (v2 >= 0 ? live_key(v2, h + 16 * half) : 0x4000u) << (16 * half);
             }
             Q1[h] = q1;
             Q2[h] = q2;
@@ -228,7 +232,7 @@ __device__ __forceinline__ void unit_init16(const KernelArgs& ka, S16& u, uint32
             Q1[h] = DEAD2;
         }
         // S(0,0) = 0 relative to T_0 = -X, window row 0
-        if (gl == 0) Q1[0] = (DEAD2 & 0xffff0000u) | live_key<G>(it.X, 0);
+        if (gl == 0) Q1[0] = (DEAD2 & 0xffff0000u) | live_key(it.X, 0);
         load_a_planes(ka, u, gl);
         u.b0 = 0u;
         u.b1 = 0u;
@@ -282,7 +286,9 @@ __device__ __forceinline__ void unit_prepare16(const KernelArgs& ka, S16& u, int
         const bool lo_ok = 2 * gl + sh < 2 * G;
         const bool hi_ok = 2 * gl + sh + 1 < 2 * G;
         const uint32_t keep = (lo_ok ? 0x0000ffffu : 0u) | (hi_ok ? 0xffff0000u : 0u);
-        const uint32_t rebase = uint32_t(16 * sh) * 0x10001u;  // row codes grow by 16*sh
+        // an odd number of half-lanes moves rows k + 16 to k (code + 16) and
+        // the next lane's rows k to k + 16 (code - 16); whole lanes keep codes
+        const uint32_t rebase = odd ? 16u - (16u << 16) : 0u;
 #pragma unroll
         for (int h = 0; h < 16; ++h) {
             uint32_t x2 = __shfl_down_sync(FULL, Q2[h], t, G);
@@ -337,8 +343,8 @@ __device__ __forceinline__ void unit_prepare16(const KernelArgs& ka, S16& u, int
                         const int r = gl * 32 + h + 16 * half;
                         const uint32_t s1 = (Q1[h] >> (16 * half)) & 0xffffu;
                         const uint32_t s2 = (Q2[h] >> (16 * half)) & 0xffffu;
-                        rec[kMigHeader + r] = s1 >= LIVE ? int((s1 - LIVE) >> P16<G>::LOG2W) : NEGU;
-                        rec[kMigHeader + W + r] = s2 >= LIVE ? int((s2 - LIVE) >> P16<G>::LOG2W) : NEGU;
+                        rec[kMigHeader + r] = s1 >= LIVE ? int((s1 - LIVE) >> LOG2KS) : NEGU;
+                        rec[kMigHeader + W + r] = s2 >= LIVE ? int((s2 - LIVE) >> LOG2KS) : NEGU;
                     }
                 }
                 if (gl == 0) {
@@ -407,17 +413,19 @@ __device__ __forceinline__ void step16(const KernelArgs& ka, S16& u, int gl, int
     uint32_t xd = __shfl_up_sync(FULL, Q2[15], 1, G);
     xu = gl == 0 ? DEAD2 : xu;
     xd = gl == 0 ? DEAD2 : xd;
-    const uint32_t U0 = __byte_perm(xu, Q1[15], 0x5432);
-    const uint32_t D0 = __byte_perm(xd, Q2[15], 0x5432);
+    // (the lower lane's row 31 has code 0 where this lane's row 0 expects
+    // code 32 from a predecessor: +32 on the low half)
+    const uint32_t U0 = __byte_perm(xu, Q1[15], 0x5432) * uint32_t(ka.one) + 32u;
+    const uint32_t D0 = __byte_perm(xd, Q2[15], 0x5432) * uint32_t(ka.one) + 32u;
     // per-step offsets in key units (the re-basing of d-1 and d-2 onto T_d),
     // both halves at once: v = o1W + max(up - 1, left, diag + SM + sub)
     const int one = ka.one;
-    const int o1W = (ka.sc.gap + u.T1 - u.T) * W;
+    const int o1W = (ka.sc.gap + u.T1 - u.T) * KS;
     const uint32_t O1 = uint32_t(o1W) * 0x10001u;
-    const int sm = (ka.sc.mismatch + u.T2 - u.T) * W - 1 - o1W;
+    const int sm = (ka.sc.mismatch + u.T2 - u.T) * KS - 1 - o1W;
     const uint32_t SM = uint32_t(sm) * 0x10001u;
     const uint32_t M1 = 0x10001u * one;  // "- M1" = minus one in both halves (IMAD)
-    const int dsw = (ka.sc.match - ka.sc.mismatch) * W;  // divisible by 2^7 for W >= 128
+    const int dsw = (ka.sc.match - ka.sc.mismatch) * KS;
     // rows of this lane inside [rlo, rhi]: bits [k0, k1) of rb
     const int i0 = u.base + gl * 32;
     const int k0 = __viaddmin_s32_relu(rlo, -i0, 32);
@@ -443,16 +451,20 @@ __device__ __forceinline__ void step16(const KernelArgs& ka, S16& u, int gl, int
         O[h] = p;
         if (h & 1) lk1 = __vimax3_u16x2(lk1, O[h - 1], p);
     }
-    // the unit's largest key and its first / last live rows
+    // the unit's largest key and its first / last live rows; a lane's key
+    // (u, code in the lane) becomes (u << log2 W) | (W - 1 - row)
     const uint32_t lkey = max(lk1 & 0xffffu, lk1 >> 16);
+    const uint32_t fkey = lkey >= LIVE ? (((lkey - LIVE) >> LOG2KS) << P16<G>::LOG2W) |
+                                             uint32_t(W - 32 - gl * 32) + (lkey & 31u)
+                                       : 0u;
     const int fr = __ffs(L) - 1, lr = 31 - __clz(L);
     const uint32_t flw = L ? (uint32_t(W - (gl * 32 + fr)) | (uint32_t(gl * 32 + lr + 1) << 16)) : 0u;
-    const uint32_t wkey = unit_max_u32<G>(lkey);
+    const uint32_t wkey = unit_max_u32<G>(fkey);
     const uint32_t fl = unit_max_u16x2<G>(flw);
     if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
     const bool uv = fl != 0u;
     if (run && uv) {
-        const int umax = int((wkey - LIVE) >> P16<G>::LOG2W);
+        const int umax = int(wkey >> P16<G>::LOG2W);
         if (umax > u.X) {  // S > best  <=>  S - T_d > X
             const int r = W - 1 - int(wkey & uint32_t(W - 1));
             u.best = u.T + umax;
@@ -538,7 +550,7 @@ __global__ void __launch_bounds__(128, 4) k_group16(KernelArgs ka, int level, in
 }  // namespace
 
 // level -> G of its packed form (32 rows per lane)
-#define LOGAN_PACKED_LEVELS(X) X(2, 4)
+#define LOGAN_PACKED_LEVELS(X) X(2, 4) X(3, 8) X(4, 16) X(5, 32)
 
 bool packed_level(int level) {
     switch (level) {
