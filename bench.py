@@ -39,18 +39,19 @@ ROOT = os.path.dirname(os.path.abspath(__file__))
 sys.path.insert(0, ROOT)
 
 METRIC = "X-drop GCUPS (computed cells), batched vs plain launch; serving p50/p99 ms"
-# From one ncu capture of the level-2 kernel (k_group<8, 16>) on the
-# 24,000-pair lognormal batch (48,000 extensions started):
+# From one ncu capture of the level-2 kernel (k_group16<4>, the packed
+# 16-bit form) on the 24,000-pair lognormal batch (48,000 extensions
+# started):
 #   bytes     dram__bytes_read.sum + dram__bytes_write.sum of the launch,
 #             scaled to a launch by the extensions it starts;
 #   fma_share the share of its executed warp instructions that issue to the
 #             FMA pipe (IMAD, from sass__inst_executed_per_opcode), the rest
 #             going to the ALU pipe or to pipes that are not near a limit.
 # Reported only while the kernel's sources are the ones captured.
-PROFILED = {"level": 2, "bytes": 114.030336e6 + 7.497472e6, "items": 48_000,
-            "fma_share": 126.0 / 347.0,
-            "sources": ("xdrop_group.cu", "logan_dev.cuh", "internal.h"),
-            "sha1": "c11e7e7940fb707e8c6dc2852623834331fe3cd4"}
+PROFILED = {"level": 2, "bytes": 113.9008e6 + 8.826368e6, "items": 48_000,
+            "fma_share": 6250213527 / 20021728734,
+            "sources": ("xdrop_group16.cu", "logan_dev.cuh", "internal.h"),
+            "sha1": "b1181c10b435ce284b396934b3b9d1a42decf8a9"}
 OPS_PER_CELL_AFFINE = 12  # Gotoh per cell: compare, diag add, E: 2 adds + max, F: 2 adds + max, 2 max, X-drop compare, select
 # The scope table's count for the linear recurrence, per cell: substitution
 # select, diag + substitution, max(up, left), + gap and max with the diagonal

@@ -524,6 +524,12 @@ int logan_get_escalation(const logan_ctx_t *ctx, int8_t *next, int n);
  * sample batch, runs the batch restricted to that class once per start
  * level (reps times, keeping the fastest), times the extension kernels with
  * CUDA events and stores the fastest level in the context's table.
+ * With the table chosen, it then times the whole pipeline on the sample
+ * (reps times each, keeping the fastest) for the two unit forms of each
+ * level -- packed 16-bit or 32-bit (LOGAN_OPT_PACKED16 1 / 0) -- crossed with
+ * the one-warp rule for small batches (LOGAN_OPT_LONG_ITEM -2 automatic /
+ * -1 several extensions per warp always), and keeps the fastest pair in the
+ * context (read back with logan_get_option).
  * Arguments as logan_extend_batch; synchronous (it waits for every run and
  * copies X_per_pair to the host).  ms_table (nullable, host float
  * [LOGAN_X_CLASSES * logan_num_levels()]) receives the measured ms, -1 for

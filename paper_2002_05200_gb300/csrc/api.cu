@@ -607,7 +607,23 @@ int load_table_json(logan_ctx_t* c, const char* path) {
             if (p == std::string::npos) return LOGAN_EINVAL;
         }
     }
-    return set_table(c, lv, kXClasses);
+    int rc = set_table(c, lv, kXClasses);
+    // optional unit-form choices of the autotuner
+    const size_t pk = text.find("\"packed16\"");
+    if (rc == LOGAN_OK && pk != std::string::npos) {
+        const size_t colon = text.find(':', pk);
+        if (colon == std::string::npos) return LOGAN_EINVAL;
+        c->packed16 = std::strtol(text.c_str() + colon + 1, nullptr, 10) ? 1 : 0;
+    }
+    const size_t li = text.find("\"long_item\"");
+    if (rc == LOGAN_OK && li != std::string::npos) {
+        const size_t colon = text.find(':', li);
+        if (colon == std::string::npos) return LOGAN_EINVAL;
+        const long long v = std::strtoll(text.c_str() + colon + 1, nullptr, 10);
+        if (v < -2) return LOGAN_EINVAL;
+        c->long_item = v;
+    }
+    return rc;
 }
 
 }  // namespace
@@ -912,10 +928,36 @@ int logan_autotune(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
         if (best_level >= 0) chosen[cls] = int8_t(best_level);
     }
     c->force_level = save_force;
-    c->opt_timing = save_timing;
-    c->opt_graphs = save_graphs;
     c->table = save_table;
     if (rc == LOGAN_OK) rc = set_table(c, chosen, kXClasses);
+    // the unit forms: packed 16-bit vs 32-bit, crossed with the one-warp
+    // rule, timed over the whole pipeline with the chosen table
+    if (rc == LOGAN_OK) {
+        const int64_t forms[4][2] = {{1, -2}, {1, -1}, {0, -2}, {0, -1}};
+        const int64_t save_packed = c->packed16, save_long = c->long_item;
+        float best_ms = -1.f;
+        int best_form = -1;
+        for (int f = 0; f < 4 && rc == LOGAN_OK; ++f) {
+            c->packed16 = forms[f][0];
+            c->long_item = forms[f][1];
+            float t_min = -1.f;
+            for (int r = 0; r < reps && rc == LOGAN_OK; ++r) {
+                rc = extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs, ws,
+                                   ws_bytes, out, stream, 0);
+                logan_stats_t st;
+                if (rc == LOGAN_OK) rc = logan_call_stats(c, 0, &st);
+                if (rc == LOGAN_OK && (t_min < 0.f || st.total_ms < t_min)) t_min = st.total_ms;
+            }
+            if (rc == LOGAN_OK && (best_form < 0 || t_min < best_ms)) {
+                best_ms = t_min;
+                best_form = f;
+            }
+        }
+        c->packed16 = best_form >= 0 ? forms[best_form][0] : save_packed;
+        c->long_item = best_form >= 0 ? forms[best_form][1] : save_long;
+    }
+    c->opt_timing = save_timing;
+    c->opt_graphs = save_graphs;
     return rc;
 }
 
@@ -928,7 +970,8 @@ int logan_autotune_save(const logan_ctx_t* c, const char* path) {
     std::fprintf(f, "{\"gpu\": \"%s\", \"sms\": %d, \"x_class_upper\": [15, 35, 75, 150, 300, 700, 2000, 536870912], \"levels\": [",
                  prop.name, prop.multiProcessorCount);
     for (int i = 0; i < kXClasses; ++i) std::fprintf(f, "%s%d", i ? ", " : "", int(c->table.lv[i]));
-    std::fprintf(f, "]}\n");
+    std::fprintf(f, "], \"packed16\": %d, \"long_item\": %lld}\n", int(c->packed16),
+                 static_cast<long long>(c->long_item));
     return std::fclose(f) == 0 ? LOGAN_OK : LOGAN_EINVAL;
 }
 

@@ -204,9 +204,14 @@ def test_autotune_table_and_roundtrip(ctx, tmp_path):
     # results with the tuned table are still exact
     ref = run_oracle(b)
     assert_same(run_gpu(ctx, b, packed2bit=True), ref, "tuned")
-    # the saved table loads back into a new context
+    # the unit forms were chosen too (packed or 32-bit, one-warp rule)
+    packed, long_item = ctx.get_option(logan.OPT_PACKED16), ctx.get_option(logan.OPT_LONG_ITEM)
+    assert packed in (0, 1) and long_item in (-2, -1)
+    # the saved table and forms load back into a new context
     c2 = logan.Context(0, autotune_json=path)
     assert c2.level_table() == table
+    assert c2.get_option(logan.OPT_PACKED16) == packed
+    assert c2.get_option(logan.OPT_LONG_ITEM) == long_item
     c2.close()
     ctx.set_level_table(before)
 
