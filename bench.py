@@ -100,6 +100,11 @@ def parse():
     ap.add_argument("--long-item", type=int, default=None,
                     help="LOGAN_OPT_LONG_ITEM for the timed calls (default: the library's "
                          "automatic rule)")
+    ap.add_argument("--autotune", type=int, default=None, choices=[0, 1],
+                    help="run logan_autotune on the workload before the timed steps (start "
+                         "level per X class, packed or 32-bit levels, one-warp rule); default "
+                         "1 for uneven_batch (its configuration has the autotuner choose) and "
+                         "uniform_pairs, 0 otherwise")
     ap.add_argument("--packed16", type=int, default=None, choices=[0, 1],
                     help="LOGAN_OPT_PACKED16 for the timed calls (default: the library's, 1)")
     ap.add_argument("--concurrent", type=int, default=1, choices=[0, 1],
@@ -984,6 +989,13 @@ def main():
         ctx.set_option(logan.OPT_LONG_ITEM, args.long_item)
     if args.packed16 is not None:
         ctx.set_option(logan.OPT_PACKED16, args.packed16)
+    tuned = None
+    if args.autotune is None:
+        args.autotune = 1 if args.workload in ("uneven_batch", "uniform_pairs") else 0
+    if args.autotune:
+        table, _ = ctx.autotune(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, reps=2)
+        tuned = {"level_table": list(table), "packed16": ctx.get_option(logan.OPT_PACKED16),
+                 "long_item": ctx.get_option(logan.OPT_LONG_ITEM)}
     stream = torch.cuda.Stream()
     ws = ctx.workspace(A, B, b.n_pairs)
     out = torch.empty((b.n_pairs, 10), dtype=torch.int32, device=f"cuda:{local}")
@@ -1094,6 +1106,8 @@ def main():
             "cells_per_step": tot_cells,
             "levels": {"ms": [round(float(v), 4) for v in level_ms],
                        "items": last["items"], "cells": last["cells"]}}
+    if tuned is not None:
+        line["autotuned"] = tuned
     if sharded:
         line["shard"] = {"pairs_this_rank": int(b.n_pairs), "pairs_total": int(full_batch.n_pairs),
                          "gathered_all_ok": ok_all}

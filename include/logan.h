@@ -181,9 +181,9 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  * + X must stay below 2^29 (else LOGAN_EINVAL for the pair).  Bands are
  * held in register windows of 64, 128, 256 and 512 rows (the first by X:
  * <= 35, <= 150, <= 300, larger); a band that outgrows 512 rows, or an X
- * above 2^20 - 4096, continues in a device-memory ring of half the
- * workspace ring's width (2^LOGAN_OPT_RING_CAP / 2 rows: 32,768 by
- * default); only a band wider than that gets status LOGAN_ERANGE.  Runs on
+ * above 2^20 - 4096, continues in the workspace's device-memory ring
+ * (2^LOGAN_OPT_RING_CAP rows: 65,536 by default); only a band of 65,536 rows
+ * or more (2^LOGAN_OPT_RING_CAP) gets status LOGAN_ERANGE.  Runs on
  * `stream` (no graphs, no timing statistics).  Returns LOGAN_EINVAL for
  * invalid scalars or pointers, LOGAN_ENOMEM if ws_bytes is too small,
  * LOGAN_ECUDA on a launch failure.
@@ -524,8 +524,10 @@ int logan_get_escalation(const logan_ctx_t *ctx, int8_t *next, int n);
  * sample batch, runs the batch restricted to that class once per start
  * level (reps times, keeping the fastest), times the extension kernels with
  * CUDA events and stores the fastest level in the context's table.
- * With the table chosen, it then times the whole pipeline on the sample
- * (reps times each, keeping the fastest) for the two unit forms of each
+ * With the table chosen, it then times the whole call on the sample as the
+ * caller runs it (the context's graph and timing options; CUDA events on
+ * `stream` around each call; one untimed call first, then reps times
+ * keeping the fastest) for the two unit forms of each
  * level -- packed 16-bit or 32-bit (LOGAN_OPT_PACKED16 1 / 0) -- crossed with
  * the one-warp rule for small batches (LOGAN_OPT_LONG_ITEM -2 automatic /
  * -1 several extensions per warp always), and keeps the fastest pair in the

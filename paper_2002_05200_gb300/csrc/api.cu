@@ -143,7 +143,9 @@ Layout make_layout(const logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t
     L.hist = take(sizeof(uint32_t) * kQueues * kBuckets);
     L.ring_cap = 1u << c->ring_log2;
     L.ring_slots = uint32_t(std::max<size_t>(1, std::min<size_t>(size_t(c->num_sms), items)));
-    L.ring = take(size_t(L.ring_slots) * 3 * L.ring_cap * sizeof(int32_t));
+    // six arrays of ring_cap cells per slot: the linear ring uses three, the
+    // affine continuation (H on three anti-diagonals, E, F on two) all six
+    L.ring = take(size_t(L.ring_slots) * 6 * L.ring_cap * sizeof(int32_t));
     L.mig_slot = take(items * sizeof(int32_t));
     for (int l = 0; l < kNumLevels; ++l) {
         const size_t rec = size_t(mig_stride(l)) * sizeof(int32_t);
@@ -931,33 +933,47 @@ int logan_autotune(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
     c->table = save_table;
     if (rc == LOGAN_OK) rc = set_table(c, chosen, kXClasses);
     // the unit forms: packed 16-bit vs 32-bit, crossed with the one-warp
-    // rule, timed over the whole pipeline with the chosen table
+    // rule, with the chosen table; each form is timed as a caller runs it
+    // (the context's own graph and timing options, one event pair around
+    // the whole call on the caller's stream), the best of `reps` after one
+    // untimed call that captures the form's graph
+    c->opt_timing = save_timing;
+    c->opt_graphs = save_graphs;
     if (rc == LOGAN_OK) {
         const int64_t forms[4][2] = {{1, -2}, {1, -1}, {0, -2}, {0, -1}};
         const int64_t save_packed = c->packed16, save_long = c->long_item;
+        cudaStream_t s = static_cast<cudaStream_t>(stream);
+        cudaEvent_t e0 = nullptr, e1 = nullptr;
+        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
+            rc = LOGAN_ECUDA;
         float best_ms = -1.f;
         int best_form = -1;
         for (int f = 0; f < 4 && rc == LOGAN_OK; ++f) {
             c->packed16 = forms[f][0];
             c->long_item = forms[f][1];
             float t_min = -1.f;
-            for (int r = 0; r < reps && rc == LOGAN_OK; ++r) {
-                rc = extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs, ws,
-                                   ws_bytes, out, stream, 0);
-                logan_stats_t st;
-                if (rc == LOGAN_OK) rc = logan_call_stats(c, 0, &st);
-                if (rc == LOGAN_OK && (t_min < 0.f || st.total_ms < t_min)) t_min = st.total_ms;
+            for (int r = -1; r < reps && rc == LOGAN_OK; ++r) {
+                if (cudaEventRecord(e0, s) != cudaSuccess) rc = LOGAN_ECUDA;
+                if (rc == LOGAN_OK)
+                    rc = extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs,
+                                       ws, ws_bytes, out, stream, 0);
+                float t = 0.f;
+                if (rc == LOGAN_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                       cudaEventSynchronize(e1) != cudaSuccess ||
+                                       cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+                    rc = LOGAN_ECUDA;
+                if (rc == LOGAN_OK && r >= 0 && (t_min < 0.f || t < t_min)) t_min = t;
             }
             if (rc == LOGAN_OK && (best_form < 0 || t_min < best_ms)) {
                 best_ms = t_min;
                 best_form = f;
             }
         }
+        if (e0) cudaEventDestroy(e0);
+        if (e1) cudaEventDestroy(e1);
         c->packed16 = best_form >= 0 ? forms[best_form][0] : save_packed;
         c->long_item = best_form >= 0 ? forms[best_form][1] : save_long;
     }
-    c->opt_timing = save_timing;
-    c->opt_graphs = save_graphs;
     return rc;
 }
 

@@ -76,6 +76,7 @@ struct S16 {
     int bi, bj;
     int m, n, X;
     unsigned long long cells, cells0;
+    uint32_t c32;  // cells of the current loop iteration, folded into cells at its top
     int64_t apos, bpos;
     int dir;
     int q0;
@@ -461,25 +462,25 @@ __device__ __forceinline__ void step16(const KernelArgs& ka, S16& u, int gl, int
     const uint32_t flw = L ? (uint32_t(W - (gl * 32 + fr)) | (uint32_t(gl * 32 + lr + 1) << 16)) : 0u;
     const uint32_t wkey = unit_max_u32<G>(fkey);
     const uint32_t fl = unit_max_u16x2<G>(flw);
-    if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
-    const bool uv = fl != 0u;
-    if (run && uv) {
-        const int umax = int(wkey >> P16<G>::LOG2W);
-        if (umax > u.X) {  // S > best  <=>  S - T_d > X
-            const int r = W - 1 - int(wkey & uint32_t(W - 1));
-            u.best = u.T + umax;
-            u.bi = u.base + r;
-            u.bj = u.d - u.bi;
-        }
-        u.T2 = u.T1;
-        u.T1 = u.T;
-        u.T = u.best - u.X;
-        u.lo = u.base + (W - int(fl & 0xffffu));
-        u.hi = u.base + int(fl >> 16) - 1;
-    } else if (u.active) {
-        u.active = false;
-        u.done = true;
-    }
+    u.c32 += run ? uint32_t(rhi - rlo + 1) : 0u;
+    // the anti-diagonal's outcome, without branches: it advances when it
+    // had a range and a live cell, else the extension ends here
+    const bool adv = run && fl != 0u;
+    const int umax = int(wkey >> P16<G>::LOG2W);
+    const bool imp = adv && umax > u.X;  // S > best  <=>  S - T_d > X
+    const int r = W - 1 - int(wkey & uint32_t(W - 1));
+    const int best = imp ? u.T + umax : u.best;
+    u.bi = imp ? u.base + r : u.bi;
+    u.bj = imp ? u.d - (u.base + r) : u.bj;
+    u.best = best;
+    const int T = u.T, T1 = u.T1;
+    u.T2 = adv ? T1 : u.T2;
+    u.T1 = adv ? T : T1;
+    u.T = adv ? best - u.X : T;
+    u.lo = adv ? u.base + (W - int(fl & 0xffffu)) : u.lo;
+    u.hi = adv ? u.base + int(fl >> 16) - 1 : u.hi;
+    u.done = u.done || (u.active && !adv);
+    u.active = u.active && adv;
     u.d += 1;
 }
 
@@ -513,8 +514,11 @@ __global__ void __launch_bounds__(128, 4) k_group16(KernelArgs ka, int level, in
     u.q0 = 0;
     u.bpre = 0u;
     u.a0 = u.a1 = u.b0 = u.b1 = 0u;
+    u.c32 = 0u;
     bool exhausted = false;
     for (;;) {
+        u.cells += u.c32;
+        u.c32 = 0u;
         if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
             if (u.done) {
                 unit_finish16(ka, u, level, gl);

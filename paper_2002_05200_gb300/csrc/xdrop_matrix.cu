@@ -21,7 +21,9 @@
 //
 // Two users:
 //  * logan_extend_batch_matrix: sequences of letter codes (one byte each,
-//    values < K), any K <= 32; every extension runs here.
+//    values < K), any K <= 32; extensions run first in register windows of
+//    64 .. 512 rows (k_mx_group below), and only bands that outgrow them, or
+//    an X too large for their keys, come here.
 //  * the affine DNA path (logan_extend_batch_affine): its register windows
 //    end at 512 rows; a band that outgrows them, or an X too large for their
 //    keys, continues here on the 2-bit pools with the 4 x 4 match / mismatch
@@ -79,9 +81,11 @@ struct MxArgs {
     const void* pb;
     const Item* items;
     ExtRes* ext;
-    const uint32_t* queue;
+    const uint32_t* queue;   // the ring's queue
     Counters* counters;
-    int q;  // queue index in counters (every entry [0, tail) is taken)
+    int q;  // the ring's queue index in counters (every entry [0, tail) is taken)
+    uint32_t* queues;        // register levels: queue l at queues + l * qcap
+    uint32_t qcap;
     const int32_t* table;  // K x K, row = letter of a; nullptr: match / mismatch
     int K;
     int match, mismatch;
@@ -208,6 +212,351 @@ __global__ void __launch_bounds__(kMxThreads) k_mx_ring(MxArgs a) {
     }
 }
 
+// ---- register windows for letter codes: several extensions per warp ----
+//
+// The affine register kernel's layout (xdrop_affine.cu) for letter codes:
+// a unit of G lanes x C rows per extension (lane g owns rows base + g*C + k
+// of a window that slides up in whole lanes), H on d-2 / d-1 / d in three
+// rotating register arrays, E and F updated in place (rows in descending
+// order), keys (H - T) * W + (W-1-row) for the best and its tie-break.  The
+// letters of a lane's rows are bytes, four to a word; the b' letters shift
+// up one row per anti-diagonal (a funnel shift per word, the lane below's
+// top letter carried in); the substitution is one shared-memory load of the
+// K x K table per cell.  A band that outgrows the window restarts at the next
+// level; after the widest it continues in the ring kernel above.
+
+constexpr int kMxLevels = 4;         // 64, 128, 256, 512 rows
+constexpr int kMxRingQueue = kMxLevels;
+constexpr int32_t kMxGroupMaxX = (1 << 20) - 4096;  // keys need (X + 1000) * W < 2^31
+
+template <int G, int C>
+struct MGroup {
+    static constexpr int W = G * C;
+    static constexpr int LOG2W = W == 64 ? 6 : W == 128 ? 7 : W == 256 ? 8 : 9;
+    static constexpr int NW = C / 4;        // letter words per lane
+    static constexpr int PREFETCH = 4 * G;  // b' letters a unit holds
+    static_assert(C % 4 == 0 && (1 << LOG2W) == W, "shape");
+};
+
+struct MState {
+    int base, lo, hi, d;
+    int best, bi, bj;
+    int m, n, X;
+    unsigned long long cells;
+    int64_t apos, bpos;
+    int dir;
+    int q0;
+    uint32_t bpre;
+    uint32_t item;
+    bool active, done, overflow;
+};
+
+// letter of stream index q (0 outside [0, len))
+__device__ __forceinline__ uint32_t mx_letter(const uint8_t* __restrict__ pool, int64_t pos,
+                                              int dir, int len, int64_t q) {
+    if (q < 0 || q >= len) return 0u;
+    return pool[pos + (dir > 0 ? q : -q)];
+}
+
+// letters of stream indices q .. q+3, q in the low byte
+__device__ __forceinline__ uint32_t mx_letters4(const uint8_t* __restrict__ pool, int64_t pos,
+                                                int dir, int len, int64_t q) {
+    return mx_letter(pool, pos, dir, len, q) | (mx_letter(pool, pos, dir, len, q + 1) << 8) |
+           (mx_letter(pool, pos, dir, len, q + 2) << 16) | (mx_letter(pool, pos, dir, len, q + 3) << 24);
+}
+
+template <int G, int C>
+__device__ __forceinline__ void mg_init(const MxArgs& a, MState& u, uint32_t id, int gl,
+                                        int (&H2)[C], int (&H1)[C], int (&E)[C], int (&F)[C],
+                                        uint32_t (&aw)[C / 4], uint32_t (&bw)[C / 4]) {
+    const Item it = a.items[id];
+    const uint8_t* pa = static_cast<const uint8_t*>(a.pa);
+    const uint8_t* pb = static_cast<const uint8_t*>(a.pb);
+    u.item = id;
+    u.apos = it.a_pos;
+    u.bpos = it.b_pos;
+    u.dir = (it.flags & ITEM_LEFT) ? -1 : 1;
+    u.m = int(it.m);
+    u.n = int(it.n);
+    u.X = it.X;
+    u.base = u.lo = u.hi = 0;
+    u.d = 1;
+    u.best = u.bi = u.bj = 0;
+    u.cells = 0ull;
+    u.q0 = 0;
+    u.bpre = mx_letters4(pb, u.bpos, u.dir, u.n, 4 * gl);
+#pragma unroll
+    for (int k = 0; k < C; ++k) H2[k] = H1[k] = E[k] = F[k] = NEGM;
+#pragma unroll
+    for (int w = 0; w < C / 4; ++w) {
+        aw[w] = mx_letters4(pa, u.apos, u.dir, u.m, int64_t(gl) * C + 4 * w - 1);
+        bw[w] = 0u;
+    }
+    if (gl == 0) H1[0] = 0;  // cell (0,0): no gap state
+    u.active = true;
+    u.done = false;
+    u.overflow = false;
+}
+
+__device__ __forceinline__ void mg_finish(const MxArgs& a, const MState& u, int level, int gl) {
+    if (gl != 0) return;
+    if (u.overflow) {
+        // the next window, after the widest the ring
+        const int nq = level + 1 < kMxLevels ? level + 1 : kMxRingQueue;
+        const unsigned int t = atomicAdd(&a.counters->tail[nq], 1u);
+        a.queues[size_t(nq) * a.qcap + t] = u.item;
+        return;
+    }
+    ExtRes r;
+    r.best = u.best;
+    r.bi = u.bi;
+    r.bj = u.bj;
+    r.status = 0;
+    r.cells = u.cells;
+    a.ext[u.item] = r;
+    atomicAdd(&a.counters->cells[level], u.cells);
+}
+
+template <int G, int C>
+__device__ __forceinline__ void mg_prepare(const MxArgs& a, MState& u, int gl, int (&H2)[C],
+                                           int (&H1)[C], int (&E)[C], int (&F)[C],
+                                           uint32_t (&aw)[C / 4], uint32_t (&bw)[C / 4]) {
+    using Gr = MGroup<G, C>;
+    const uint8_t* pa = static_cast<const uint8_t*>(a.pa);
+    const uint8_t* pb = static_cast<const uint8_t*>(a.pb);
+    const int rlo = max(u.lo, u.d - u.n);
+    const int top = min(u.hi + 3, u.m);
+    const bool need = u.active && top >= u.base + Gr::W;
+    if (__any_sync(FULL, need)) {
+        const int s = need ? (rlo - 1 - u.base) / C : 0;
+        const bool ovf = need && (s <= 0 || top >= u.base + s * C + Gr::W);
+        const int sh = (need && !ovf) ? s : 0;
+#pragma unroll
+        for (int k = 0; k < C; ++k) {
+            H2[k] = __shfl_down_sync(FULL, H2[k], sh, G);
+            H1[k] = __shfl_down_sync(FULL, H1[k], sh, G);
+            E[k] = __shfl_down_sync(FULL, E[k], sh, G);
+            F[k] = __shfl_down_sync(FULL, F[k], sh, G);
+        }
+#pragma unroll
+        for (int w = 0; w < C / 4; ++w) {
+            aw[w] = __shfl_down_sync(FULL, aw[w], sh, G);
+            bw[w] = __shfl_down_sync(FULL, bw[w], sh, G);
+        }
+        u.base += sh * C;
+        if (sh > 0 && gl >= G - sh) {
+            const int i0 = u.base + gl * C;
+#pragma unroll
+            for (int k = 0; k < C; ++k) H2[k] = H1[k] = E[k] = F[k] = NEGM;
+#pragma unroll
+            for (int w = 0; w < C / 4; ++w) {
+                aw[w] = mx_letters4(pa, u.apos, u.dir, u.m, int64_t(i0) + 4 * w - 1);
+                // b' letters as of anti-diagonal d-1: index (d-1) - i - 1, row order
+                uint32_t v = 0u;
+#pragma unroll
+                for (int t = 0; t < 4; ++t)
+                    v |= mx_letter(pb, u.bpos, u.dir, u.n, int64_t(u.d) - 2 - (i0 + 4 * w + t))
+                         << (8 * t);
+                bw[w] = v;
+            }
+        }
+        if (ovf) {
+            u.active = false;
+            u.done = true;
+            u.overflow = true;
+        }
+    }
+    const int q = u.d - u.base - 1;  // the next three steps read q .. q+2
+    const bool refill = u.active && (q < u.q0 || q + 2 >= u.q0 + Gr::PREFETCH);
+    if (__any_sync(FULL, refill)) {
+        if (refill) {
+            u.q0 = q;
+            u.bpre = mx_letters4(pb, u.bpos, u.dir, u.n, int64_t(q) + 4 * gl);
+        }
+    }
+}
+
+template <int G>
+__device__ __forceinline__ int mg_unit_max(int v) {
+    if constexpr (G == 32) {
+        return __reduce_max_sync(FULL, v);
+    } else {
+#pragma unroll
+        for (int o = G / 2; o >= 1; o >>= 1) v = max(v, __shfl_xor_sync(FULL, v, o, G));
+        return v;
+    }
+}
+
+// one anti-diagonal of every unit of the warp: H2 / H1 = H on d-2 / d-1, HO
+// receives H on d; E and F on d-1 are replaced by those of d
+template <int G, int C>
+__device__ __forceinline__ void mg_step(const MxArgs& a, const int* tab, MState& u, int gl,
+                                        int unit, const int (&H2)[C], const int (&H1)[C],
+                                        int (&HO)[C], int (&E)[C], int (&F)[C],
+                                        const uint32_t (&aw)[C / 4], uint32_t (&bw)[C / 4]) {
+    using Gr = MGroup<G, C>;
+    const int rlo = max(u.lo, u.d - u.n);
+    const int rhi = min(u.hi + 1, u.m);
+    const bool run = u.active && rlo <= rhi;
+    // b' letters move up one row; window row 0 takes stream index d - base - 1
+    const int qq = u.d - u.base - 1 - u.q0;
+    const uint32_t pre = __shfl_sync(FULL, u.bpre, unit * G + ((qq >> 2) & (G - 1)));
+    const uint32_t front = (pre >> (8u * uint32_t(qq & 3))) & 0xffu;
+    uint32_t carry = __shfl_up_sync(FULL, bw[C / 4 - 1], 1, G);
+    carry = gl == 0 ? (front << 24) : carry;
+#pragma unroll
+    for (int w = C / 4 - 1; w >= 1; --w) bw[w] = __funnelshift_l(bw[w - 1], bw[w], 8);
+    bw[0] = __funnelshift_l(carry, bw[0], 8);
+    int h1c = __shfl_up_sync(FULL, H1[C - 1], 1, G);
+    int f1c = __shfl_up_sync(FULL, F[C - 1], 1, G);
+    int h2c = __shfl_up_sync(FULL, H2[C - 1], 1, G);
+    if (gl == 0) h1c = f1c = h2c = NEGM;
+    const int T = u.best - u.X;
+    const int goe = a.go + a.ge;
+    const int i0 = u.base + gl * C;
+    const int k0 = __viaddmin_s32_relu(rlo, -i0, C);
+    const int k1 = __viaddmin_s32_relu(rhi, 1 - i0, C);
+    const uint32_t rb = __funnelshift_lc(~0u, 0u, k1) & ~__funnelshift_lc(~0u, 0u, k0);
+    const uint32_t kbase = uint32_t(C - 1) - uint32_t(T) * uint32_t(Gr::W);
+    int lkey = -1;
+    uint32_t bits = 0u;
+#pragma unroll
+    for (int k = C - 1; k >= 0; --k) {  // descending: F[k-1] still holds d-1
+        const int uh = k ? H1[k - 1] : h1c;
+        const int uf = k ? F[k - 1] : f1c;
+        const int dg = k ? H2[k - 1] : h2c;
+        const int e = __vimax3_s32(E[k] + a.ge, H1[k] + goe, NEGM);
+        const int f = __vimax3_s32(uf + a.ge, uh + goe, NEGM);
+        const uint32_t la = (aw[k >> 2] >> (8 * (k & 3))) & 0xffu;
+        const uint32_t lb = (bw[k >> 2] >> (8 * (k & 3))) & 0xffu;
+        const int h = __vimax3_s32(dg + tab[la * uint32_t(a.K) + lb], e, f);
+        const bool live = ((rb >> k) & 1u) && h >= T;
+        HO[k] = live ? h : NEGM;
+        E[k] = live ? e : NEGM;
+        F[k] = live ? f : NEGM;
+        // live: 0 <= h - T <= X + max entry, so the key stays below 2^31
+        lkey = max(lkey, live ? int(uint32_t(h) * uint32_t(Gr::W) + (kbase - uint32_t(k))) : -1);
+        bits = (bits << 1) | (live ? 1u : 0u);
+    }
+    if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
+    const int wkey = mg_unit_max<G>(lkey >= 0 ? lkey + (G - 1 - gl) * C : -1);
+    int rfirst, rlast;
+    if constexpr (G == 32) {
+        rfirst = __reduce_min_sync(FULL, bits ? gl * C + (__ffs(bits) - 1) : Gr::W);
+        rlast = __reduce_max_sync(FULL, bits ? gl * C + (31 - __clz(bits)) : -1);
+    } else {
+        const uint32_t vote = __ballot_sync(FULL, bits != 0u);
+        const uint32_t uvv = (vote >> (unit * G)) & ((1u << G) - 1u);
+        const int fl = uvv ? __ffs(uvv) - 1 : 0, ll = uvv ? 31 - __clz(uvv) : 0;
+        const uint32_t fb = __shfl_sync(FULL, bits, unit * G + fl);
+        const uint32_t lb = __shfl_sync(FULL, bits, unit * G + ll);
+        rfirst = uvv ? fl * C + (__ffs(fb) - 1) : Gr::W;
+        rlast = uvv ? ll * C + (31 - __clz(lb)) : -1;
+    }
+    if (run && rlast >= 0) {
+        const int hmax = T + (wkey >> Gr::LOG2W);
+        if (hmax > u.best) {
+            u.best = hmax;
+            u.bi = u.base + Gr::W - 1 - (wkey & (Gr::W - 1));
+            u.bj = u.d - u.bi;
+        }
+        u.lo = u.base + rfirst;
+        u.hi = u.base + rlast;
+    } else if (u.active) {
+        u.active = false;
+        u.done = true;
+    }
+    u.d += 1;
+}
+
+template <int G, int C>
+__global__ void __launch_bounds__(128, 4) k_mx_group(MxArgs a, int level) {
+    __shared__ int tab[kMaxK * kMaxK];
+    for (int t = threadIdx.x; t < a.K * a.K; t += blockDim.x) tab[t] = a.table[t];
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G, unit = lane / G;
+    const uint32_t* q = a.queues + size_t(level) * a.qcap;
+    int P0[C], P1[C], P2[C], E[C], F[C];
+    uint32_t aw[C / 4], bw[C / 4];
+#pragma unroll
+    for (int k = 0; k < C; ++k) P0[k] = P1[k] = P2[k] = E[k] = F[k] = NEGM;
+#pragma unroll
+    for (int w = 0; w < C / 4; ++w) aw[w] = bw[w] = 0u;
+    MState u;
+    u.active = u.done = u.overflow = false;
+    u.item = 0u;
+    u.m = u.n = 0;
+    u.base = u.lo = u.hi = 0;
+    u.d = 1;
+    u.best = u.bi = u.bj = 0;
+    u.X = 0;
+    u.cells = 0ull;
+    u.apos = u.bpos = 0;
+    u.dir = 1;
+    u.q0 = 0;
+    u.bpre = 0u;
+    bool exhausted = false;
+    for (;;) {
+        if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
+            if (u.done) {
+                mg_finish(a, u, level, gl);
+                u.done = false;
+            }
+            const bool need = !u.active && !exhausted;
+            uint32_t id = 0xffffffffu;
+            const uint32_t want = __ballot_sync(FULL, need && gl == 0);
+            if (want) {
+                const int leader = __ffs(want) - 1;
+                // levels run one after another, so a level's queue is complete
+                unsigned int first = 0u, limit = 0u;
+                if (lane == leader) {
+                    first = atomicAdd(&a.counters->head[level], unsigned(__popc(want)));
+                    limit = a.counters->tail[level];
+                }
+                first = __shfl_sync(FULL, first, leader);
+                limit = __shfl_sync(FULL, limit, leader);
+                const unsigned int slot = first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
+                if (need && slot < limit) id = q[slot];
+            }
+            if (need) {
+                if (id != 0xffffffffu) mg_init<G, C>(a, u, id, gl, P0, P1, E, F, aw, bw);
+                else exhausted = true;
+            }
+        }
+        if (!__any_sync(FULL, u.active)) break;
+        mg_prepare<G, C>(a, u, gl, P0, P1, E, F, aw, bw);
+        mg_step<G, C>(a, tab, u, gl, unit, P0, P1, P2, E, F, aw, bw);
+        mg_step<G, C>(a, tab, u, gl, unit, P1, P2, P0, E, F, aw, bw);
+        mg_step<G, C>(a, tab, u, gl, unit, P2, P0, P1, E, F, aw, bw);
+    }
+}
+
+#define LOGAN_MX_LEVELS(X) X(0, 8, 8) X(1, 16, 8) X(2, 32, 8) X(3, 32, 16)
+
+cudaError_t launch_mx_level(int level, const MxArgs& a, int grid, cudaStream_t s) {
+    switch (level) {
+#define CASE(L, G, C) case L: k_mx_group<G, C><<<grid, 128, 0, s>>>(a, L); break;
+        LOGAN_MX_LEVELS(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int mx_level_blocks(int level) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (level) {
+#define CASE(L, G, C) \
+    case L: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mx_group<G, C>, 128, 0); break;
+        LOGAN_MX_LEVELS(CASE)
+#undef CASE
+        default: break;
+    }
+    return e == cudaSuccess ? std::max(1, n) : 1;
+}
+
 // ---- the matrix call's own pre-processing ----
 
 // per sequence: 1 if a letter code is >= K
@@ -238,7 +587,7 @@ struct MxPool {
 __global__ void k_mx_split(MxPool A, MxPool B, const uint32_t* __restrict__ seeds, uint32_t n_pairs,
                            const int32_t* __restrict__ table, int K, int64_t big, int32_t X,
                            const int32_t* __restrict__ Xs, Item* items, PairInfo* info, ExtRes* ext,
-                           uint32_t* queue, Counters* counters) {
+                           uint32_t* queues, uint32_t qcap, Counters* counters) {
     const uint32_t p = blockIdx.x * blockDim.x + threadIdx.x;
     if (p >= n_pairs) return;
     const uint32_t ia = seeds[5 * p], ib = seeds[5 * p + 1];
@@ -283,8 +632,12 @@ __global__ void k_mx_split(MxPool A, MxPool B, const uint32_t* __restrict__ seed
     items[2 * p] = L;
     items[2 * p + 1] = R;
     info[p] = PairInfo{seed, 0};
-    if (!(L.flags & ITEM_SKIP)) queue[atomicAdd(&counters->tail[0], 1u)] = 2 * p;
-    if (!(R.flags & ITEM_SKIP)) queue[atomicAdd(&counters->tail[0], 1u)] = 2 * p + 1;
+    // the narrowest register window first; an X too large for its keys
+    // goes straight to the ring
+    const int q = x > kMxGroupMaxX ? kMxRingQueue : 0;
+    uint32_t* queue = queues + size_t(q) * qcap;
+    if (!(L.flags & ITEM_SKIP)) queue[atomicAdd(&counters->tail[q], 1u)] = 2 * p;
+    if (!(R.flags & ITEM_SKIP)) queue[atomicAdd(&counters->tail[q], 1u)] = 2 * p + 1;
 }
 
 __global__ void k_mx_reset(Counters* c) {
@@ -317,7 +670,7 @@ MxLayout mx_layout(int num_sms, const logan_seqs_t* A, const logan_seqs_t* B, ui
     L.items = take(items * sizeof(Item));
     L.ext = take(items * sizeof(ExtRes));
     L.info = take(size_t(n) * sizeof(PairInfo));
-    L.queue = take(items * sizeof(uint32_t));
+    L.queue = take(size_t(kMxLevels + 1) * items * sizeof(uint32_t));
     L.counters = take(sizeof(Counters));
     L.badA = take(A->count);
     L.badB = take(B->count);
@@ -349,10 +702,11 @@ cudaError_t launch_affine_ring(const KernelArgs& ka, int q, int go, int ge, int 
     a.mismatch = ka.sc.mismatch;
     a.go = go;
     a.ge = ge;
+    a.queues = nullptr;
+    a.qcap = 0;
     a.ring = ka.ring;
-    // the workspace ring holds 3 * ring_cap cells per slot; six arrays fit
-    // at half that width
-    a.cap = ka.ring_cap / 2;
+    // the workspace ring holds 6 * ring_cap cells per slot
+    a.cap = ka.ring_cap;
     a.cells_level = kNumLevels;
     k_mx_ring<false><<<grid, kMxThreads, 0, s>>>(a);
     return cudaGetLastError();
@@ -451,9 +805,10 @@ extern "C" int logan_extend_batch_matrix(logan_ctx_t* ctx, const logan_seqs_t* s
                                        : MxPool{static_cast<const uint8_t*>(seqsB->bases),
                                                 seqsB->offsets, seqsB->lengths, seqsB->count,
                                                 badB};
+                const uint32_t qcap = 2u * n_pairs;
                 k_mx_split<<<(n_pairs + 255) / 256, 256, 0, s>>>(
                     pa, pb, reinterpret_cast<const uint32_t*>(seeds), n_pairs, table, K, big, X,
-                    X_per_pair, items, info, ext, queue, counters);
+                    X_per_pair, items, info, ext, queue, qcap, counters);
                 e = cudaGetLastError();
                 if (e == cudaSuccess) {
                     MxArgs a;
@@ -461,9 +816,11 @@ extern "C" int logan_extend_batch_matrix(logan_ctx_t* ctx, const logan_seqs_t* s
                     a.pb = pb.bases;
                     a.items = items;
                     a.ext = ext;
-                    a.queue = queue;
+                    a.queues = queue;
+                    a.qcap = qcap;
+                    a.queue = queue + size_t(kMxRingQueue) * qcap;
                     a.counters = counters;
-                    a.q = 0;
+                    a.q = kMxRingQueue;
                     a.table = table;
                     a.K = K;
                     a.match = 0;
@@ -472,9 +829,15 @@ extern "C" int logan_extend_batch_matrix(logan_ctx_t* ctx, const logan_seqs_t* s
                     a.ge = gap_extend;
                     a.ring = reinterpret_cast<int32_t*>(ws + L.ring);
                     a.cap = 1u << LOGAN_MATRIX_RING_LOG2;
-                    a.cells_level = 0;
-                    k_mx_ring<true><<<L.slots, kMxThreads, 0, s>>>(a);
-                    e = cudaGetLastError();
+                    a.cells_level = kMxRingQueue;
+                    // register windows of 64 .. 512 rows, narrowest first,
+                    // then the ring for what outgrew them
+                    for (int l = 0; l < kMxLevels && e == cudaSuccess; ++l)
+                        e = launch_mx_level(l, a, sms * mx_level_blocks(l), s);
+                    if (e == cudaSuccess) {
+                        k_mx_ring<true><<<L.slots, kMxThreads, 0, s>>>(a);
+                        e = cudaGetLastError();
+                    }
                 }
                 if (e == cudaSuccess) e = launch_combine(seeds, info, ext, n_pairs, out, s);
             }

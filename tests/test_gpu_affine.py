@@ -108,29 +108,37 @@ def test_uneven_pairs_x500_no_erange(ctx):
                 "uneven, X = 500")
 
 
-def test_band_beyond_the_ring_reports_erange(ctx):
-    # identical 40 kbp sequences at X = 2^20: the unpruned band outgrows the
-    # ring's 32,768 rows -> LOGAN_ERANGE for that pair, the others exact
+def test_band_of_65535_rows_and_beyond(ctx):
+    # identical sequences at X = 2^20 leave the band unpruned: 50,000 letters
+    # stay inside the ring's 65,536 rows (closed form: L * match at (L, L)
+    # over all (L+1)^2 - 1 cells); 66,000 letters outgrow it -> LOGAN_ERANGE
+    # for that pair; the other pairs are exact
     rng = np.random.default_rng(12)
-    seq = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, 40_000)]
+    L0, L1 = 50_000, 66_000
+    s0 = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, L0)]
+    s1 = np.frombuffer(b"ACGT", np.uint8)[rng.integers(0, 4, L1)]
     base = synth.uniform_pairs(n_pairs=8, length=1200, seed=13)
-    poolA = np.concatenate([seq, base.poolA])
-    poolB = np.concatenate([seq, base.poolB])
-    offA = np.concatenate([[0], base.offA.astype(np.int64) + 40_000]).astype(np.uint64)
-    offB = np.concatenate([[0], base.offB.astype(np.int64) + 40_000]).astype(np.uint64)
-    lenA = np.concatenate([[40_000], base.lenA]).astype(np.uint32)
-    lenB = np.concatenate([[40_000], base.lenB]).astype(np.uint32)
-    seeds = np.zeros(9, dtype=base.seeds.dtype)
-    seeds[0] = (0, 0, 0, 0, 0)
-    seeds[1:] = base.seeds
-    seeds["idxA"][1:] += 1
-    seeds["idxB"][1:] += 1
-    Xs = np.full(9, 50, np.int32)
-    Xs[0] = 1 << 20
+    poolA = np.concatenate([s0, s1, base.poolA])
+    poolB = np.concatenate([s0, s1, base.poolB])
+    offA = np.concatenate([[0, L0], base.offA.astype(np.int64) + L0 + L1]).astype(np.uint64)
+    offB = np.concatenate([[0, L0], base.offB.astype(np.int64) + L0 + L1]).astype(np.uint64)
+    lenA = np.concatenate([[L0, L1], base.lenA]).astype(np.uint32)
+    lenB = np.concatenate([[L0, L1], base.lenB]).astype(np.uint32)
+    seeds = np.zeros(10, dtype=base.seeds.dtype)
+    seeds[1] = (1, 1, 0, 0, 0)
+    seeds[2:] = base.seeds
+    seeds["idxA"][2:] += 2
+    seeds["idxB"][2:] += 2
+    Xs = np.full(10, 50, np.int32)
+    Xs[:2] = 1 << 20
     b = synth.Batch("ring_limit", poolA, offA, lenA, poolB, offB, lenB, seeds, 50, Xs)
     g = run_affine(ctx, b, -2, -1)
-    assert g["status"][0] == logan.ERANGE
-    assert_same(g[1:], ref_affine(b.subset(np.arange(1, 9)), -2, -1), "the other pairs")
+    assert g["status"][0] == logan.OK
+    assert (g["score"][0], g["left"][0], g["right"][0]) == (L0 * b.match, 0, L0 * b.match)
+    assert (g["begA"][0], g["endA"][0], g["begB"][0], g["endB"][0]) == (0, L0, 0, L0)
+    assert g["cells"][0] == (L0 + 1) ** 2 - 1
+    assert g["status"][1] == logan.ERANGE
+    assert_same(g[2:], ref_affine(b.subset(np.arange(2, 10)), -2, -1), "the other pairs")
 
 
 def test_argument_errors(ctx):

@@ -71,6 +71,18 @@ def test_dna_matrix_equals_affine_path(ctx, go, ge):
     assert np.array_equal(logan.results_to_numpy(aff), g)
 
 
+def test_wide_bands_escalate_through_every_window(ctx):
+    # unpruned bands up to 1500 rows: each register window (64, 128, 256, 512
+    # rows) hands its overflows to the next, the widest to the ring
+    rng = np.random.default_rng(17)
+    M = rng.integers(-3, 4, size=(12, 12)).astype(np.int32)
+    b = synth.tiny_pairs(40, 1500, seed=18, X_choices=(100_000,))
+    b.poolA = rng.integers(0, 12, size=b.poolA.size).astype(np.uint8)
+    b.poolB = rng.integers(0, 12, size=b.poolB.size).astype(np.uint8)
+    assert_same(run_matrix(ctx, b, M, -2, -1), oracle.run_batch_matrix(b, M, -2, -1)[0],
+                "bands up to 1500 rows")
+
+
 def test_invalid_inputs(ctx):
     import torch
     b = synth.protein_pairs(40, lo=30, hi=200, seed=5)
