@@ -520,23 +520,26 @@ int logan_set_escalation(logan_ctx_t *ctx, const int8_t *next, int n);
 int logan_get_escalation(const logan_ctx_t *ctx, int8_t *next, int n);
 
 /* Autotuner (the paper schedules threads in proportion to X, Sec. IV-B; here
- * the unit per X class is measured): for every X class present in the
- * sample batch, runs the batch restricted to that class once per start
- * level (reps times, keeping the fastest), times the extension kernels with
- * CUDA events and stores the fastest level in the context's table.
- * With the table chosen, it then times the whole call on the sample as the
- * caller runs it (the context's graph and timing options; CUDA events on
- * `stream` around each call; one untimed call first, then reps times
- * keeping the fastest) for the two unit forms of each
- * level -- packed 16-bit or 32-bit (LOGAN_OPT_PACKED16 1 / 0) -- crossed with
- * the one-warp rule for small batches (LOGAN_OPT_LONG_ITEM -2 automatic /
- * -1 several extensions per warp always), and keeps the fastest pair in the
- * context (read back with logan_get_option).
+ * the unit per X class is measured).  Every configuration is timed as a
+ * caller runs it: the context's graph and timing options, one CUDA event
+ * pair around the whole call on `stream`, one untimed call first (it
+ * captures the configuration's graph), then the fastest of `reps` calls.
+ * First, the start level of every X class present in the sample batch: one
+ * pass of coordinate descent over the classes, each trying every level on
+ * the whole sample with the other classes at their current choice; a level
+ * replaces the class's current one only when the batch ran faster with it.
+ * With the table chosen, the
+ * whole sample runs for the two unit forms of each level -- packed 16-bit
+ * or 32-bit (LOGAN_OPT_PACKED16 1 / 0) -- crossed with the one-warp rule for
+ * small batches (LOGAN_OPT_LONG_ITEM -2 automatic / -1 several extensions
+ * per warp always), and the fastest pair stays in the context (read back
+ * with logan_get_option).
  * Arguments as logan_extend_batch; synchronous (it waits for every run and
  * copies X_per_pair to the host).  ms_table (nullable, host float
- * [LOGAN_X_CLASSES * logan_num_levels()]) receives the measured ms, -1 for
- * classes absent from the sample.  The context's other options are
- * restored afterwards. */
+ * [LOGAN_X_CLASSES * logan_num_levels()]) receives the first stage's
+ * whole-sample ms of each class at each level, -1 for classes absent from
+ * the sample.  The context's other
+ * options are restored afterwards. */
 int logan_autotune(logan_ctx_t *ctx, const logan_seqs_t *seqsA, const logan_seqs_t *seqsB,
                    const logan_seed_t *seeds, uint32_t n_pairs, int32_t match, int32_t mismatch,
                    int32_t gap, int32_t X, const int32_t *X_per_pair, void *workspace,

@@ -209,7 +209,6 @@ void default_table(LevelTable& t) {
     const int8_t lv[kXClasses] = {0, 1, 2, 2, 3, 4, 6, 7};
     for (int i = 0; i < kXClasses; ++i) t.lv[i] = lv[i];
     t.max_level = kNumLevels - 1;
-    t.only_xclass = -1;
 }
 
 int launch_unit(logan_ctx* c, int u, const KernelArgs& ka, int phase, cudaStream_t s,
@@ -356,7 +355,6 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
         // rejected
         const int8_t alv[kXClasses] = {0, 0, 1, 1, 2, 3, 3, 3};
         for (int i = 0; i < kXClasses; ++i) tab.lv[i] = alv[i];
-        tab.only_xclass = -1;
         tab.long_min = 0xffffffffu;
     }
     int first = 0;
@@ -421,7 +419,7 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     // above that level (a level only receives items from narrower ones).
     uint32_t start_units = ~0u;
     int first_escalated = plain ? first + 1 : 0;
-    if (!plain && !Xs && tab.only_xclass < 0) {
+    if (!plain && !Xs) {
         const int64_t forced_start = c->force_level >= 0 ? c->force_level : -1;
         int l = forced_start >= 0 ? int(forced_start) : int(tab.lv[x_class(X)]);
         if (X > kGroupMaxX && l < kWarpLevels) l = kWarpLevels;
@@ -891,89 +889,89 @@ int logan_autotune(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
     } else {
         present[x_class(X)] = true;
     }
-    const int64_t save_force = c->force_level, save_timing = c->opt_timing,
-                  save_graphs = c->opt_graphs;
+    const int64_t save_packed = c->packed16, save_long = c->long_item;
     const LevelTable save_table = c->table;
     const int maxl = int(c->max_level);
-    c->opt_timing = 1;
-    c->opt_graphs = 0;
-    int rc = LOGAN_OK;
+    cudaStream_t s = static_cast<cudaStream_t>(stream);
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    int rc = (cudaEventCreate(&e0) == cudaSuccess && cudaEventCreate(&e1) == cudaSuccess)
+                 ? LOGAN_OK
+                 : LOGAN_ECUDA;
+    // one configuration, timed as a caller runs it: the context's graph and
+    // timing options, an event pair around the whole call on the caller's
+    // stream; one untimed call first (it captures the configuration's
+    // graph), then the fastest of `reps`
+    auto time_call = [&](float* best) {
+        float t_min = -1.f;
+        for (int r = -1; r < reps && rc == LOGAN_OK; ++r) {
+            if (cudaEventRecord(e0, s) != cudaSuccess) rc = LOGAN_ECUDA;
+            if (rc == LOGAN_OK)
+                rc = extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs, ws,
+                                   ws_bytes, out, stream, 0);
+            float t = 0.f;
+            if (rc == LOGAN_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
+                                   cudaEventSynchronize(e1) != cudaSuccess ||
+                                   cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
+                rc = LOGAN_ECUDA;
+            if (rc == LOGAN_OK && r >= 0 && (t_min < 0.f || t < t_min)) t_min = t;
+        }
+        *best = t_min;
+    };
     int8_t chosen[kXClasses];
     for (int k = 0; k < kXClasses; ++k) chosen[k] = save_table.lv[k];
     if (ms_table)
         for (int k = 0; k < kXClasses * kNumLevels; ++k) ms_table[k] = -1.f;
+    // the start level of each X class present: one pass of coordinate
+    // descent on the whole sample -- every level for one class, the other
+    // classes at their current choice -- so that a level replaces a class's
+    // current one (itself a candidate) only when the whole batch ran faster
+    // with it
     for (int cls = 0; cls < kXClasses && rc == LOGAN_OK; ++cls) {
         if (!present[cls]) continue;
-        c->table.only_xclass = cls;
         float best_ms = 0.f;
         int best_level = -1;
         for (int lvl = 0; lvl <= maxl && rc == LOGAN_OK; ++lvl) {
-            c->force_level = lvl;
-            float t_min = -1.f;
-            for (int r = 0; r < reps && rc == LOGAN_OK; ++r) {
-                rc = extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs, ws,
-                                   ws_bytes, out, stream, 0);
-                logan_stats_t st;
-                if (rc == LOGAN_OK) rc = logan_call_stats(c, 0, &st);
-                if (rc != LOGAN_OK) break;
-                float t = st.level_ms[kNumLevels];
-                for (int l = 0; l <= maxl; ++l) t += st.level_ms[l];
-                if (t_min < 0.f || t < t_min) t_min = t;
-            }
+            int8_t trial[kXClasses];
+            for (int k = 0; k < kXClasses; ++k) trial[k] = chosen[k];
+            trial[cls] = int8_t(lvl);
+            rc = set_table(c, trial, kXClasses);
+            float t = -1.f;
+            if (rc == LOGAN_OK) time_call(&t);
             if (rc != LOGAN_OK) break;
-            if (ms_table) ms_table[cls * kNumLevels + lvl] = t_min;
-            if (best_level < 0 || t_min < best_ms) {
-                best_ms = t_min;
+            if (ms_table) ms_table[cls * kNumLevels + lvl] = t;
+            if (best_level < 0 || t < best_ms) {
+                best_ms = t;
                 best_level = lvl;
             }
         }
         if (best_level >= 0) chosen[cls] = int8_t(best_level);
     }
-    c->force_level = save_force;
     c->table = save_table;
     if (rc == LOGAN_OK) rc = set_table(c, chosen, kXClasses);
-    // the unit forms: packed 16-bit vs 32-bit, crossed with the one-warp
-    // rule, with the chosen table; each form is timed as a caller runs it
-    // (the context's own graph and timing options, one event pair around
-    // the whole call on the caller's stream), the best of `reps` after one
-    // untimed call that captures the form's graph
-    c->opt_timing = save_timing;
-    c->opt_graphs = save_graphs;
+    // the unit forms with the chosen table: packed 16-bit vs 32-bit, crossed
+    // with the one-warp rule
     if (rc == LOGAN_OK) {
         const int64_t forms[4][2] = {{1, -2}, {1, -1}, {0, -2}, {0, -1}};
-        const int64_t save_packed = c->packed16, save_long = c->long_item;
-        cudaStream_t s = static_cast<cudaStream_t>(stream);
-        cudaEvent_t e0 = nullptr, e1 = nullptr;
-        if (cudaEventCreate(&e0) != cudaSuccess || cudaEventCreate(&e1) != cudaSuccess)
-            rc = LOGAN_ECUDA;
         float best_ms = -1.f;
         int best_form = -1;
         for (int f = 0; f < 4 && rc == LOGAN_OK; ++f) {
             c->packed16 = forms[f][0];
             c->long_item = forms[f][1];
-            float t_min = -1.f;
-            for (int r = -1; r < reps && rc == LOGAN_OK; ++r) {
-                if (cudaEventRecord(e0, s) != cudaSuccess) rc = LOGAN_ECUDA;
-                if (rc == LOGAN_OK)
-                    rc = extend_common(c, A, B, seeds, n_pairs, match, mismatch, gap, X, Xs,
-                                       ws, ws_bytes, out, stream, 0);
-                float t = 0.f;
-                if (rc == LOGAN_OK && (cudaEventRecord(e1, s) != cudaSuccess ||
-                                       cudaEventSynchronize(e1) != cudaSuccess ||
-                                       cudaEventElapsedTime(&t, e0, e1) != cudaSuccess))
-                    rc = LOGAN_ECUDA;
-                if (rc == LOGAN_OK && r >= 0 && (t_min < 0.f || t < t_min)) t_min = t;
-            }
-            if (rc == LOGAN_OK && (best_form < 0 || t_min < best_ms)) {
-                best_ms = t_min;
+            float t = -1.f;
+            time_call(&t);
+            if (rc == LOGAN_OK && (best_form < 0 || t < best_ms)) {
+                best_ms = t;
                 best_form = f;
             }
         }
-        if (e0) cudaEventDestroy(e0);
-        if (e1) cudaEventDestroy(e1);
         c->packed16 = best_form >= 0 ? forms[best_form][0] : save_packed;
         c->long_item = best_form >= 0 ? forms[best_form][1] : save_long;
+    } else {
+        c->packed16 = save_packed;
+        c->long_item = save_long;
     }
+    if (e0) cudaEventDestroy(e0);
+    if (e1) cudaEventDestroy(e1);
     return rc;
 }
 

@@ -116,7 +116,6 @@ constexpr int kBuckets = 128;
 struct LevelTable {
     int8_t lv[8];
     int max_level;
-    int only_xclass;
     // items with m + n >= long_min that start below level kTwinLevels go to
     // that level's one-warp form (0xffffffff: none)
     uint32_t long_min;

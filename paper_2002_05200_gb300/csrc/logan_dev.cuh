@@ -113,16 +113,36 @@ constexpr int PHASE_INITIAL = 0;
 constexpr int PHASE_ESCALATED = 1;
 constexpr int PHASE_PLAIN = 2;
 
-// n consecutive slots of queue `q` for this phase: returns the first; those
-// at or past *limit are used up.
-__device__ __forceinline__ unsigned int pop_slots(Counters* c, int q, int phase, unsigned int n,
-                                                  unsigned int* limit) {
-    if (phase == PHASE_INITIAL) {
-        *limit = c->started[q];
-        return atomicAdd(&c->head[q], n);
+// Queue slot of each idle unit of a warp (the units whose leader lane is set
+// in `want`; `unit` is this lane's unit of G lanes).  A warp's first call in
+// a launch takes static slots -- unit u of the launch's warp w gets entry
+// u * warps + w of the phase's range -- so the first entries (the longest:
+// binning orders a queue longest first) go one to a warp, in launch order,
+// before any warp gets a second, which spreads them over the SMs and their
+// schedulers instead of leaving it to the order in which warps reach an
+// atomic; later calls pop dynamically after the static entries.  Every unit
+// must be idle at the first call (true at kernel start).  Returns the slot;
+// one at or past `limit` means the range is used up.
+template <int G>
+__device__ __forceinline__ unsigned int pop_unit_slot(Counters* c, int q, int phase, uint32_t want,
+                                                      int lane, int unit, bool& first_wave,
+                                                      unsigned int& limit) {
+    constexpr unsigned int U = 32 / G;
+    const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
+    const unsigned int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
+    const unsigned int lo = phase == PHASE_INITIAL ? 0u : c->started[q];
+    limit = phase == PHASE_INITIAL ? c->started[q] : c->tail[q];
+    if (first_wave) {
+        first_wave = false;
+        return lo + unsigned(unit) * nwarps + gw;
     }
-    *limit = c->tail[q];
-    return c->started[q] + atomicAdd(&c->head2[q], n);
+    const int leader = __ffs(want) - 1;
+    unsigned int first = 0u;
+    if (lane == leader)
+        first = atomicAdd(phase == PHASE_INITIAL ? &c->head[q] : &c->head2[q],
+                          unsigned(__popc(want)));
+    first = __shfl_sync(0xffffffffu, first, leader);
+    return lo + U * nwarps + first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
 }
 
 // Next slot of queue `q` for this phase, or ~0u when the range is used up.

@@ -136,17 +136,16 @@ __device__ __forceinline__ int work_bucket(uint32_t m, uint32_t n) {
 // starting level of an item, or -1 when the X-class filter leaves it out
 __device__ __forceinline__ int item_level(const Item& it, LevelTable table, int force, int maxl) {
     const int xc = x_class(it.X);
-    if (table.only_xclass >= 0 && xc != table.only_xclass) return -1;
     int l = force >= 0 ? force : int(table.lv[xc]);
     if (it.X > kGroupMaxX && l < kWarpLevels) l = kWarpLevels;
     return min(l, maxl);
 }
 
 // queue of an item: its starting level, or that level's latency form for a
-// long item; -1 when the X-class filter leaves it out
+// long item
 __device__ __forceinline__ int item_queue(const Item& it, LevelTable table, int force, int maxl) {
     const int l = item_level(it, table, force, maxl);
-    if (l >= 0 && l < kTwinLevels && uint64_t(it.m) + it.n >= table.long_min) return twin_queue(l);
+    if (l < kTwinLevels && uint64_t(it.m) + it.n >= table.long_min) return twin_queue(l);
     return l;
 }
 
@@ -159,7 +158,6 @@ __global__ void k_bin_hist(const Item* __restrict__ items, uint32_t n, LevelTabl
         const Item it = items[i];
         if (it.flags & ITEM_SKIP) continue;
         const int q = item_queue(it, table, force, maxl);
-        if (q < 0) continue;
         atomicAdd(&h[q * kBuckets + (kBuckets - 1 - work_bucket(it.m, it.n))], 1u);
     }
     __syncthreads();
@@ -206,7 +204,6 @@ __global__ void k_bin_scatter(const Item* __restrict__ items, uint32_t n, LevelT
     const Item it = items[i];
     if (it.flags & ITEM_SKIP) return;
     const int q = item_queue(it, table, force, maxl);
-    if (q < 0) return;
     const uint32_t pos = atomicAdd(&cursor[q * kBuckets + (kBuckets - 1 - work_bucket(it.m, it.n))], 1u);
     queues[size_t(q) * qcap + pos] = i;
 }

@@ -468,6 +468,7 @@ __global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) 
     u.q0 = 0;
     u.bpre = u.aw = u.bw = 0u;
     bool exhausted = false;
+    bool first_wave = true;  // the warp's first pop takes static slots
     for (;;) {
         if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
             if (u.done) {
@@ -487,14 +488,9 @@ __global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) 
                 // costs the same whether its units are busy or idle)
                 const uint32_t want = __ballot_sync(FULL, need && gl == 0);
                 if (want) {
-                    const int leader = __ffs(want) - 1;
-                    unsigned int first = 0u, limit = 0u;
-                    if (lane == leader)
-                        first = pop_slots(ka.counters, queue, phase, unsigned(__popc(want)), &limit);
-                    first = __shfl_sync(FULL, first, leader);
-                    limit = __shfl_sync(FULL, limit, leader);
-                    const unsigned int slot =
-                        first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
+                    unsigned int limit = 0u;
+                    const unsigned int slot = pop_unit_slot<G>(ka.counters, queue, phase, want,
+                                                               lane, unit, first_wave, limit);
                     if (need && slot < limit) id = q[slot];
                 }
             }

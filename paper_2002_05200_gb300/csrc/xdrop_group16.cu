@@ -516,6 +516,7 @@ __global__ void __launch_bounds__(128, 4) k_group16(KernelArgs ka, int level, in
     u.a0 = u.a1 = u.b0 = u.b1 = 0u;
     u.c32 = 0u;
     bool exhausted = false;
+    bool first_wave = true;  // the warp's first pop takes static slots
     for (;;) {
         u.cells += u.c32;
         u.c32 = 0u;
@@ -529,13 +530,9 @@ __global__ void __launch_bounds__(128, 4) k_group16(KernelArgs ka, int level, in
             // one pop per warp for all of its idle units
             const uint32_t want = __ballot_sync(FULL, need && gl == 0);
             if (want) {
-                const int leader = __ffs(want) - 1;
-                unsigned int first = 0u, limit = 0u;
-                if (lane == leader)
-                    first = pop_slots(ka.counters, queue, phase, unsigned(__popc(want)), &limit);
-                first = __shfl_sync(FULL, first, leader);
-                limit = __shfl_sync(FULL, limit, leader);
-                const unsigned int slot = first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
+                unsigned int limit = 0u;
+                const unsigned int slot =
+                    pop_unit_slot<G>(ka.counters, queue, phase, want, lane, unit, first_wave, limit);
                 if (need && slot < limit) id = q[slot];
             }
             if (need) {
