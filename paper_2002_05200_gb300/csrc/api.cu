@@ -277,7 +277,7 @@ uint32_t packed16_levels(const logan_ctx* c, Scoring sc, int32_t X, const int32_
     const int64_t mp = std::max<int64_t>(sc.match, 0);
     const int64_t ag = -int64_t(sc.gap), am = sc.mismatch < 0 ? -int64_t(sc.mismatch) : sc.mismatch;
     uint32_t mask = 0u;
-    for (int l = 0; l < kWarpLevels; ++l) {
+    for (int l = 0; l < kNumLevels; ++l) {
         if (!packed_level(l) || l > tab.max_level) continue;
         int64_t xmax = 0;
         if (!Xs && force < 0) {

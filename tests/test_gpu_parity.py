@@ -346,9 +346,10 @@ def test_packed16_bounds_select_the_32bit_form(ctx):
 
 
 @pytest.mark.parametrize("packed16", [0, 1])
-@pytest.mark.parametrize("level", [2, 3, 4, 5])
+@pytest.mark.parametrize("level", [2, 3, 4, 5, 6])
 def test_packed16_every_level(ctx, level, packed16):
-    # every packed level (windows of 128, 256, 512 and 1024 rows) started
+    # every packed level (windows of 128, 256, 512, 1024 and 2048 rows, the
+    # last with two 32-row virtual lanes per lane) started
     # directly; narrower bands stay, wider ones escalate to the next level
     # (band-state records in both directions between packed and 32-bit
     # levels); scalar X so that the bound holds for the forced level
@@ -363,3 +364,34 @@ def test_packed16_every_level(ctx, level, packed16):
     assert bool(st["packed_levels"] & (1 << level)) == bool(packed16), st["packed_levels"]
     assert st["items"][level] > 0
     assert_same(g, ref, f"level {level}, packed16={packed16}")
+
+
+def test_packed_wide_bands_through_levels_5_6_7(ctx):
+    # free gaps (gap 0) on unrelated random pairs give bands of 1,000 to
+    # 3,000 rows at X = 240, a bound the packed forms still hold; started at
+    # the 1024-row level, the bands move with band-state records to the
+    # 2048-row packed level (two virtual lanes per lane, slides of 16-row
+    # halves in every phase) and past it to the 4096-row level
+    rng = np.random.default_rng(29)
+    n = 24
+    lenA = rng.integers(6_000, 12_001, size=n).astype(np.uint32)
+    lenB = (lenA.astype(np.int64) + rng.integers(-200, 201, size=n)).astype(np.uint32)
+    alpha = np.frombuffer(b"ACGT", np.uint8)
+    poolA = alpha[rng.integers(0, 4, int(lenA.sum()))]
+    poolB = alpha[rng.integers(0, 4, int(lenB.sum()))]
+    offA = np.concatenate([[0], np.cumsum(lenA.astype(np.int64))[:-1]]).astype(np.uint64)
+    offB = np.concatenate([[0], np.cumsum(lenB.astype(np.int64))[:-1]]).astype(np.uint64)
+    seeds = np.zeros(n, dtype=synth.SEED_DTYPE)
+    seeds["idxA"] = seeds["idxB"] = np.arange(n, dtype=np.uint32)
+    b = synth.Batch("free_gaps", poolA, offA, lenA, poolB, offB, lenB, seeds, 240)
+    b.match, b.mismatch, b.gap = 1, -1, 0
+    ref = run_oracle(b)
+    ctx.set_option(logan.OPT_FORCE_LEVEL, 5)
+    ctx.set_option(logan.OPT_PACKED16, 1)
+    ctx.set_option(logan.OPT_LONG_ITEM, -1)
+    ctx.set_option(logan.OPT_TIMING, 1)
+    g = run_gpu(ctx, b)
+    st = ctx.last_stats()
+    assert st["packed_levels"] & (1 << 5) and st["packed_levels"] & (1 << 6), st["packed_levels"]
+    assert st["items"][6] > 0 and st["items"][7] > 0, st["items"]
+    assert_same(g, ref, "free gaps, levels 5-7")
