@@ -116,13 +116,15 @@ constexpr int PHASE_PLAIN = 2;
 // Queue slot of each idle unit of a warp (the units whose leader lane is set
 // in `want`; `unit` is this lane's unit of G lanes).  A warp's first call in
 // a launch takes static slots -- unit u of the launch's warp w gets entry
-// u * warps + w of the phase's range -- so the first entries (the longest:
-// binning orders a queue longest first) go one to a warp, in launch order,
-// before any warp gets a second, which spreads them over the SMs and their
-// schedulers instead of leaving it to the order in which warps reach an
-// atomic; later calls pop dynamically after the static entries.  Every unit
-// must be idle at the first call (true at kernel start).  Returns the slot;
-// one at or past `limit` means the range is used up.
+// w * (32 / G) + u of the phase's range -- so the first entries (the
+// longest: binning orders a queue longest first) go to the warps in launch
+// order, and with them to the SMs and their schedulers in turn (a block's
+// warps sit on one SM's four schedulers, consecutive blocks on different
+// SMs), instead of following the order in which warps reach an atomic;
+// consecutive entries share a warp, so its units start on items of similar
+// length.  Later calls pop dynamically after the static entries.  Every
+// unit must be idle at the first call (true at kernel start).  Returns the
+// slot; one at or past `limit` means the range is used up.
 template <int G>
 __device__ __forceinline__ unsigned int pop_unit_slot(Counters* c, int q, int phase, uint32_t want,
                                                       int lane, int unit, bool& first_wave,
@@ -134,7 +136,7 @@ __device__ __forceinline__ unsigned int pop_unit_slot(Counters* c, int q, int ph
     limit = phase == PHASE_INITIAL ? c->started[q] : c->tail[q];
     if (first_wave) {
         first_wave = false;
-        return lo + unsigned(unit) * nwarps + gw;
+        return lo + gw * U + unsigned(unit);
     }
     const int leader = __ffs(want) - 1;
     unsigned int first = 0u;

@@ -74,6 +74,7 @@ struct UState {
     int m, n, X;
     unsigned long long cells;
     unsigned long long cells0;  // cells computed before this level (resumed items)
+    uint32_t c32;               // cells of the current loop iteration, folded into cells at its top
     int64_t apos, bpos;
     int dir;
     int q0;          // first b' stream index held in the unit's prefetch words
@@ -388,7 +389,11 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
     for (int c = 1; c < NCH; ++c) lkey = max(lkey, lk[c]);
     // live rows of this lane; bit C-1-k <-> row k
     const uint32_t bits = ~dead & Gr::ALLC;
-    if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
+    if constexpr (C >= 32) {  // (the 32-row lanes are short of registers)
+        if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
+    } else {
+        u.c32 += run ? uint32_t(rhi - rlo + 1) : 0u;
+    }
     // the unit's first and last live window rows (W / -1 when none) and its
     // largest key
     int rfirst, rlast;
@@ -407,26 +412,47 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
         rfirst = uvv ? fl * C + (__clz(fb) - (32 - C)) : Gr::W;
         rlast = uvv ? ll * C + (C - __ffs(lb)) : -1;
     }
-    const bool uv = rlast >= 0;
-    if (run && uv) {
-        // best: largest key = highest relative score, smallest row on ties
-        const int umax = wkey >> Gr::LOG2W;
-        if (umax > u.X) {  // S > best  <=>  S - T_d > X
-            const int r = Gr::W - 1 - (wkey & (Gr::W - 1));
-            u.best = u.T + umax;
-            u.bi = u.base + r;
-            u.bj = u.d - u.bi;
+    // the anti-diagonal's outcome: it advances when it had a range and a
+    // live cell, else the extension ends here.  The best: largest key =
+    // highest relative score, smallest row on ties
+    if constexpr (C >= 32) {
+        // (branches: the 32-row lanes are short of registers)
+        if (run && rlast >= 0) {
+            const int umax = wkey >> Gr::LOG2W;
+            if (umax > u.X) {  // S > best  <=>  S - T_d > X
+                const int r = Gr::W - 1 - (wkey & (Gr::W - 1));
+                u.best = u.T + umax;
+                u.bi = u.base + r;
+                u.bj = u.d - u.bi;
+            }
+            u.T2 = u.T1;
+            u.T1 = u.T;
+            u.T = u.best - u.X;
+            u.lo = u.base + rfirst;
+            u.hi = u.base + rlast;
+        } else if (u.active) {
+            u.active = false;
+            u.done = true;
         }
-        u.T2 = u.T1;
-        u.T1 = u.T;
-        u.T = u.best - u.X;
-        u.lo = u.base + rfirst;
-        u.hi = u.base + rlast;
-    } else if (u.active) {
-        // empty range or no live cell: the extension ends here
-        u.active = false;
-        u.done = true;
+        u.d += 1;
+        return;
     }
+    const bool adv = run && rlast >= 0;
+    const int umax = wkey >> Gr::LOG2W;
+    const bool imp = adv && umax > u.X;  // S > best  <=>  S - T_d > X
+    const int r = Gr::W - 1 - (wkey & (Gr::W - 1));
+    const int best = imp ? u.T + umax : u.best;
+    u.bi = imp ? u.base + r : u.bi;
+    u.bj = imp ? u.d - (u.base + r) : u.bj;
+    u.best = best;
+    const int T = u.T, T1 = u.T1;
+    u.T2 = adv ? T1 : u.T2;
+    u.T1 = adv ? T : T1;
+    u.T = adv ? best - u.X : T;
+    u.lo = adv ? u.base + rfirst : u.lo;
+    u.hi = adv ? u.base + rlast : u.hi;
+    u.done = u.done || (u.active && !adv);
+    u.active = u.active && adv;
     u.d += 1;
 }
 
@@ -463,6 +489,7 @@ __global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) 
     u.cells = 0ull;
     u.cells0 = 0ull;
     u.migrated = false;
+    u.c32 = 0u;
     u.apos = u.bpos = 0;
     u.dir = 1;
     u.q0 = 0;
@@ -470,6 +497,10 @@ __global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) 
     bool exhausted = false;
     bool first_wave = true;  // the warp's first pop takes static slots
     for (;;) {
+        if constexpr (C < 32) {
+            u.cells += u.c32;
+            u.c32 = 0u;
+        }
         if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
             if (u.done) {
                 unit_finish(ka, u, level, gl, twin);

@@ -660,7 +660,7 @@ __global__ void __launch_bounds__(128, V == 1 ? 4 : 3)
 }  // namespace
 
 // level -> (G, V) of its packed form: G lanes of V virtual lanes of 32 rows
-#define LOGAN_PACKED_LEVELS(X) X(2, 4, 1) X(3, 8, 1) X(4, 16, 1) X(5, 32, 1) X(6, 32, 2)
+#define LOGAN_PACKED_LEVELS(X) X(2, 4, 1) X(3, 8, 1) X(4, 16, 1) X(5, 16, 2) X(6, 32, 2)
 
 bool packed_level(int level) {
     switch (level) {
