@@ -112,6 +112,7 @@ struct Counters {
 constexpr int PHASE_INITIAL = 0;
 constexpr int PHASE_ESCALATED = 1;
 constexpr int PHASE_PLAIN = 2;
+constexpr int PHASE_WHOLE = 3;  // every entry [0, tail): levels that run one after another
 
 // Queue slot of each idle unit of a warp (the units whose leader lane is set
 // in `want`; `unit` is this lane's unit of G lanes).  A warp's first call in
@@ -132,7 +133,7 @@ __device__ __forceinline__ unsigned int pop_unit_slot(Counters* c, int q, int ph
     constexpr unsigned int U = 32 / G;
     const unsigned int nwarps = gridDim.x * (blockDim.x >> 5);
     const unsigned int gw = blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5);
-    const unsigned int lo = phase == PHASE_INITIAL ? 0u : c->started[q];
+    const unsigned int lo = phase == PHASE_ESCALATED ? c->started[q] : 0u;
     limit = phase == PHASE_INITIAL ? c->started[q] : c->tail[q];
     if (first_wave) {
         first_wave = false;
@@ -141,7 +142,7 @@ __device__ __forceinline__ unsigned int pop_unit_slot(Counters* c, int q, int ph
     const int leader = __ffs(want) - 1;
     unsigned int first = 0u;
     if (lane == leader)
-        first = atomicAdd(phase == PHASE_INITIAL ? &c->head[q] : &c->head2[q],
+        first = atomicAdd(phase == PHASE_ESCALATED ? &c->head2[q] : &c->head[q],
                           unsigned(__popc(want)));
     first = __shfl_sync(0xffffffffu, first, leader);
     return lo + U * nwarps + first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));

@@ -49,6 +49,7 @@ struct AState {
     int best, bi, bj;
     int m, n, X;
     unsigned long long cells;
+    uint32_t c32;  // cells of the current loop iteration, folded into cells at its top
     int64_t apos, bpos;
     int dir;
     int q0;
@@ -253,7 +254,7 @@ __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, ASt
         }
         lkey = __vimax3_s32(lkey, key[0], key[1]);
     }
-    if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
+    u.c32 += run ? uint32_t(rhi - rlo + 1) : 0u;
     const int wkey = a_unit_max<G>(lkey >= 0 ? lkey + (G - 1 - gl) * C : -1);
     int rfirst, rlast;
     if constexpr (G == 32) {
@@ -268,19 +269,19 @@ __device__ __forceinline__ void a_step(const KernelArgs& ka, int go, int ge, ASt
         rfirst = uvv ? fl * C + (__ffs(fb) - 1) : Gr::W;
         rlast = uvv ? ll * C + (31 - __clz(lb)) : -1;
     }
-    if (run && rlast >= 0) {
-        const int hmax = T + (wkey >> Gr::LOG2W);
-        if (hmax > u.best) {  // strict: the first anti-diagonal reaching it
-            u.best = hmax;
-            u.bi = u.base + Gr::W - 1 - (wkey & (Gr::W - 1));
-            u.bj = u.d - u.bi;
-        }
-        u.lo = u.base + rfirst;
-        u.hi = u.base + rlast;
-    } else if (u.active) {
-        u.active = false;  // empty range or no live cell
-        u.done = true;
-    }
+    // the anti-diagonal's outcome, without branches: it advances when it had
+    // a range and a live cell, else the extension ends here
+    const bool adv = run && rlast >= 0;
+    const int hmax = T + (wkey >> Gr::LOG2W);
+    const bool imp = adv && hmax > u.best;  // strict: the first anti-diagonal reaching it
+    const int r = u.base + Gr::W - 1 - (wkey & (Gr::W - 1));
+    u.bi = imp ? r : u.bi;
+    u.bj = imp ? u.d - r : u.bj;
+    u.best = imp ? hmax : u.best;
+    u.lo = adv ? u.base + rfirst : u.lo;
+    u.hi = adv ? u.base + rlast : u.hi;
+    u.done = u.done || (u.active && !adv);
+    u.active = u.active && adv;
     u.d += 1;
 }
 
@@ -306,8 +307,12 @@ __global__ void __launch_bounds__(128, 4) k_affine(KernelArgs ka, int go, int ge
     u.dir = 1;
     u.q0 = 0;
     u.bpre = u.aw = u.bw = 0u;
+    u.c32 = 0u;
     bool exhausted = false;
+    bool first_wave = true;  // the warp's first pop takes static slots
     for (;;) {
+        u.cells += u.c32;
+        u.c32 = 0u;
         if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
             if (u.done) {
                 a_finish(ka, u, level, gl, n_levels);
@@ -317,17 +322,11 @@ __global__ void __launch_bounds__(128, 4) k_affine(KernelArgs ka, int go, int ge
             uint32_t id = 0xffffffffu;
             const uint32_t want = __ballot_sync(FULL, need && gl == 0);
             if (want) {
-                const int leader = __ffs(want) - 1;
                 // levels run one after another, so a level's queue (its
                 // binned items, then those escalated into it) is complete
-                unsigned int first = 0u, limit = 0u;
-                if (lane == leader) {
-                    first = atomicAdd(&ka.counters->head[level], unsigned(__popc(want)));
-                    limit = ka.counters->tail[level];
-                }
-                first = __shfl_sync(FULL, first, leader);
-                limit = __shfl_sync(FULL, limit, leader);
-                const unsigned int slot = first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
+                unsigned int limit = 0u;
+                const unsigned int slot = pop_unit_slot<G>(ka.counters, level, PHASE_WHOLE, want,
+                                                           lane, unit, first_wave, limit);
                 if (need && slot < limit) id = q[slot];
             }
             if (need) {

@@ -243,6 +243,7 @@ struct MState {
     int best, bi, bj;
     int m, n, X;
     unsigned long long cells;
+    uint32_t c32;  // cells of the current loop iteration, folded into cells at its top
     int64_t apos, bpos;
     int dir;
     int q0;
@@ -438,7 +439,11 @@ __device__ __forceinline__ void mg_step(const MxArgs& a, const int* tab, MState&
         lkey = max(lkey, live ? int(uint32_t(h) * uint32_t(Gr::W) + (kbase - uint32_t(k))) : -1);
         bits = (bits << 1) | (live ? 1u : 0u);
     }
-    if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
+    if constexpr (C >= 16) {  // (the 16-row lanes are short of registers)
+        if (run) u.cells += (unsigned long long)(rhi - rlo + 1);
+    } else {
+        u.c32 += run ? uint32_t(rhi - rlo + 1) : 0u;
+    }
     const int wkey = mg_unit_max<G>(lkey >= 0 ? lkey + (G - 1 - gl) * C : -1);
     int rfirst, rlast;
     if constexpr (G == 32) {
@@ -453,24 +458,41 @@ __device__ __forceinline__ void mg_step(const MxArgs& a, const int* tab, MState&
         rfirst = uvv ? fl * C + (__ffs(fb) - 1) : Gr::W;
         rlast = uvv ? ll * C + (31 - __clz(lb)) : -1;
     }
-    if (run && rlast >= 0) {
-        const int hmax = T + (wkey >> Gr::LOG2W);
-        if (hmax > u.best) {
-            u.best = hmax;
-            u.bi = u.base + Gr::W - 1 - (wkey & (Gr::W - 1));
-            u.bj = u.d - u.bi;
+    // the anti-diagonal's outcome: it advances when it had a range and a live
+    // cell, else the extension ends here
+    if constexpr (C >= 16) {  // (branches: the 16-row lanes are short of registers)
+        if (run && rlast >= 0) {
+            const int hmax = T + (wkey >> Gr::LOG2W);
+            if (hmax > u.best) {
+                u.best = hmax;
+                u.bi = u.base + Gr::W - 1 - (wkey & (Gr::W - 1));
+                u.bj = u.d - u.bi;
+            }
+            u.lo = u.base + rfirst;
+            u.hi = u.base + rlast;
+        } else if (u.active) {
+            u.active = false;
+            u.done = true;
         }
-        u.lo = u.base + rfirst;
-        u.hi = u.base + rlast;
-    } else if (u.active) {
-        u.active = false;
-        u.done = true;
+        u.d += 1;
+        return;
     }
+    const bool adv = run && rlast >= 0;
+    const int hmax = T + (wkey >> Gr::LOG2W);
+    const bool imp = adv && hmax > u.best;  // strict: the first anti-diagonal reaching it
+    const int r = u.base + Gr::W - 1 - (wkey & (Gr::W - 1));
+    u.bi = imp ? r : u.bi;
+    u.bj = imp ? u.d - r : u.bj;
+    u.best = imp ? hmax : u.best;
+    u.lo = adv ? u.base + rfirst : u.lo;
+    u.hi = adv ? u.base + rlast : u.hi;
+    u.done = u.done || (u.active && !adv);
+    u.active = u.active && adv;
     u.d += 1;
 }
 
 template <int G, int C>
-__global__ void __launch_bounds__(128, 4) k_mx_group(MxArgs a, int level) {
+__global__ void __launch_bounds__(128, C >= 16 ? 3 : 4) k_mx_group(MxArgs a, int level) {
     __shared__ int tab[kMaxK * kMaxK];
     for (int t = threadIdx.x; t < a.K * a.K; t += blockDim.x) tab[t] = a.table[t];
     __syncthreads();
@@ -496,8 +518,14 @@ __global__ void __launch_bounds__(128, 4) k_mx_group(MxArgs a, int level) {
     u.dir = 1;
     u.q0 = 0;
     u.bpre = 0u;
+    u.c32 = 0u;
     bool exhausted = false;
+    bool first_wave = true;  // the warp's first pop takes static slots
     for (;;) {
+        if constexpr (C < 16) {
+            u.cells += u.c32;
+            u.c32 = 0u;
+        }
         if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
             if (u.done) {
                 mg_finish(a, u, level, gl);
@@ -507,16 +535,10 @@ __global__ void __launch_bounds__(128, 4) k_mx_group(MxArgs a, int level) {
             uint32_t id = 0xffffffffu;
             const uint32_t want = __ballot_sync(FULL, need && gl == 0);
             if (want) {
-                const int leader = __ffs(want) - 1;
                 // levels run one after another, so a level's queue is complete
-                unsigned int first = 0u, limit = 0u;
-                if (lane == leader) {
-                    first = atomicAdd(&a.counters->head[level], unsigned(__popc(want)));
-                    limit = a.counters->tail[level];
-                }
-                first = __shfl_sync(FULL, first, leader);
-                limit = __shfl_sync(FULL, limit, leader);
-                const unsigned int slot = first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
+                unsigned int limit = 0u;
+                const unsigned int slot = pop_unit_slot<G>(a.counters, level, PHASE_WHOLE, want,
+                                                           lane, unit, first_wave, limit);
                 if (need && slot < limit) id = q[slot];
             }
             if (need) {
