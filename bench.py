@@ -1113,7 +1113,10 @@ def main():
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "strong" if sharded else "weak",
             "vs_baseline": None,
-            "dtype": "int32", "data": "synthetic",
+            # the packed levels compute in 16-bit halves (two cells per
+            # 32-bit register) where the score bound holds, the rest in int32
+            "dtype": "int16x2+int32" if int(last.get("packed_levels", 0)) else "int32",
+            "data": "synthetic",
             "config": cfg,
             "clocks": clocks, "gpu_launches": launches * args.steps,
             "cells_per_step": tot_cells,

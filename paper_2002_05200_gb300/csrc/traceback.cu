@@ -28,6 +28,7 @@
 //     joins the left codes, the seed and the right codes.
 // Same cell update and range rules as the extension kernels, so the sweep
 // meets the same best cells.
+#include <cub/device/device_radix_sort.cuh>
 #include <cub/device/device_scan.cuh>
 
 #include <algorithm>
@@ -53,8 +54,9 @@ constexpr int kTbWarps = kTbThreads / 32;
 constexpr int kWarpCap = 512;
 constexpr int kSmemCap = 2048;
 constexpr int TB_WIDE = 1;       // status: retry in the device-memory ring
-constexpr int TB_WARP_WIDE = 2;  // status: retry on a block
+constexpr int TB_WARP_WIDE = 2;  // status: wide from the start, swept by a block
 constexpr int TB_BOUND = 3;      // status: the codes outgrew the item's words (not expected)
+constexpr int TB_OUTGREW = 4;    // status: outgrew a warp's ring, retry on a block
 
 struct TbRed {
     int mx, first, last;
@@ -76,7 +78,8 @@ __device__ __forceinline__ TbRed tb_reduce(TbRed v, TbRed* sh) {
 }
 
 struct TbItem {  // per item: its best cell and the recording sweep's status
-    int32_t bi, bj, status, pad;
+    int32_t bi, bj, status;
+    int32_t wide;  // swept by a block from the start (the warp sweep leaves it alone)
 };
 
 struct TbArgs {
@@ -89,6 +92,8 @@ struct TbArgs {
     uint64_t* ad_word;         // per anti-diagonal: first word
     uint64_t n_words;          // size of codes (reads beyond it are refused)
     unsigned long long* cells; // nullable: cells of the completed sweeps
+    const uint32_t* order;     // item ids, the most code words first
+    unsigned int* next;        // pop cursors into order: [0] warps, [1] and [2] the block passes
 };
 
 // The sweep of one item up to its best anti-diagonal by TW threads (a warp,
@@ -138,7 +143,7 @@ __device__ void tb_record(const TbArgs& t, uint32_t id, int32_t* R, int cap, TbR
         if (rlo > rhi) break;
         const int width = rhi - rlo + 1;
         if (width + 2 > cap) {
-            status = TW == 32 ? TB_WARP_WIDE : cap < int(ka.ring_cap) ? TB_WIDE : LOGAN_ERANGE;
+            status = TW == 32 ? TB_OUTGREW : cap < int(ka.ring_cap) ? TB_WIDE : LOGAN_ERANGE;
             break;
         }
         const uint64_t nw = uint64_t(width + 15) >> 4;
@@ -215,30 +220,44 @@ __device__ void tb_record(const TbArgs& t, uint32_t id, int32_t* R, int cap, TbR
     }
 }
 
-// The recording sweep, one item per warp.
+// The recording sweep, one item per warp; warps pop the items, the largest
+// first, so that the sweep does not end on a few warps holding several long
+// items each while the rest of the GPU idles.
 __global__ void __launch_bounds__(kTbThreads) k_tb_record_warp(TbArgs t) {
     __shared__ int32_t wring[kTbWarps][3 * kWarpCap];
     const int w = int(threadIdx.x >> 5);
-    const uint32_t nw = gridDim.x * uint32_t(kTbWarps);
-    for (uint32_t id = blockIdx.x * uint32_t(kTbWarps) + uint32_t(w); id < t.ka.n_items;
-         id += nw) {
+    for (;;) {
+        unsigned int slot = 0u;
+        if ((threadIdx.x & 31u) == 0u) slot = atomicAdd(&t.next[0], 1u);
+        slot = __shfl_sync(FULL, slot, 0);
+        if (slot >= t.ka.n_items) break;
+        const uint32_t id = t.order[slot];
         const TbItem x = t.info[id];
-        if (x.status || x.bi + x.bj == 0) continue;
+        if (x.wide || x.status || x.bi + x.bj == 0) continue;
         tb_record<32>(t, id, wring[w], kWarpCap, nullptr);
         __syncwarp();
     }
 }
 
-// The items whose band outgrew a warp's ring, one per block: 2048 rows in
-// shared memory, else the block's slice of the device-memory ring.
-__global__ void __launch_bounds__(kTbThreads) k_tb_record_block(TbArgs t) {
+// The items of status `which`, one per block: 2048 rows in shared memory,
+// else the block's slice of the device-memory ring.  Two passes: the items
+// wide from the start (TB_WARP_WIDE, beside the warp sweep, which leaves
+// them alone), then those that outgrew a warp's ring (TB_OUTGREW).
+__global__ void __launch_bounds__(kTbThreads) k_tb_record_block(TbArgs t, int which, int cursor) {
     __shared__ TbRed sh[kTbWarps];
     __shared__ int32_t sring[3 * kSmemCap];
     __shared__ int s_wide;
+    __shared__ unsigned int s_slot;
     int32_t* R = t.ka.ring + size_t(blockIdx.x) * 3u * t.ka.ring_cap;
     const int gcap = int(t.ka.ring_cap);
-    for (uint32_t id = blockIdx.x; id < t.ka.n_items; id += gridDim.x) {
-        if (t.info[id].status != TB_WARP_WIDE) continue;
+    for (;;) {
+        if (threadIdx.x == 0) s_slot = atomicAdd(&t.next[cursor], 1u);
+        __syncthreads();
+        const unsigned int slot = s_slot;
+        __syncthreads();
+        if (slot >= t.ka.n_items) break;
+        const uint32_t id = t.order[slot];
+        if (t.info[id].status != which) continue;
         const bool fits = gcap > kSmemCap;
         if (fits) tb_record<kTbThreads>(t, id, sring, kSmemCap, sh);
         __syncthreads();
@@ -270,8 +289,10 @@ __global__ void k_tb_prepare(const Item* __restrict__ items, const ExtRes* __res
             // from the start (a warp would outgrow its ring)
             const Item it = items[id];
             if (!st && dstar &&
-                uint64_t(e.cells) > uint64_t(kWarpCap / 2) * (uint64_t(it.m) + uint64_t(it.n)))
+                uint64_t(e.cells) > uint64_t(kWarpCap / 2) * (uint64_t(it.m) + uint64_t(it.n))) {
                 x.status = TB_WARP_WIDE;
+                x.wide = 1;
+            }
             info[id] = x;
             // anti-diagonals 1..d* hold at most the extension's cells, each
             // starting on a word
@@ -281,6 +302,11 @@ __global__ void k_tb_prepare(const Item* __restrict__ items, const ExtRes* __res
         }
         pair_codes[p] = codes + seeds[5 * p + 4];
     }
+}
+
+__global__ void k_tb_iota(uint32_t* __restrict__ ids, uint32_t n) {
+    const uint32_t i = blockIdx.x * blockDim.x + threadIdx.x;
+    if (i < n) ids[i] = i;
 }
 
 // predecessor code of the cell in row i of the anti-diagonal whose table
@@ -395,7 +421,14 @@ struct TbScratch {
     cudaStream_t s;
     std::vector<void*> ptrs;
     bool ok = true;
-    explicit TbScratch(cudaStream_t st) : s(st) {}
+    // a second stream and its fork / join events, for the concurrent sweeps
+    cudaStream_t aux = nullptr;
+    cudaEvent_t fork = nullptr, join = nullptr;
+    explicit TbScratch(cudaStream_t st) : s(st) {
+        ok = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) == cudaSuccess &&
+             cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
+             cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
+    }
     template <typename T>
     T* get(size_t n) {
         void* p = nullptr;
@@ -407,7 +440,12 @@ struct TbScratch {
         return static_cast<T*>(p);
     }
     ~TbScratch() {
+        // (after an error between the fork and the join, aux may still run)
+        if (aux) cudaStreamSynchronize(aux);
         for (void* p : ptrs) cudaFreeAsync(p, s);
+        if (join) cudaEventDestroy(join);
+        if (fork) cudaEventDestroy(fork);
+        if (aux) cudaStreamDestroy(aux);
     }
 };
 
@@ -497,6 +535,22 @@ int run_traceback(int num_sms, const ExtensionViews& v, const logan_seed_t* seed
     uint64_t* ad_word = S.get<uint64_t>(total_ads);
     if (clk.on) clk.dcells = S.get<unsigned long long>(1);
     if (!S.ok) return LOGAN_ENOMEM;
+    // the recording sweeps pop the items the most code words first
+    uint32_t* ids = S.get<uint32_t>(n_items);
+    uint32_t* order = S.get<uint32_t>(n_items);
+    uint64_t* keys = S.get<uint64_t>(n_items);
+    unsigned int* next = S.get<unsigned int>(3);
+    size_t sort_bytes = 0;
+    cub::DeviceRadixSort::SortPairsDescending(nullptr, sort_bytes, iw, keys, ids, order,
+                                              int(n_items), 0, 64, s);
+    void* sort_tmp = S.get<char>(sort_bytes);
+    if (!S.ok) return LOGAN_ENOMEM;
+    k_tb_iota<<<(n_items + 255) / 256, 256, 0, s>>>(ids, n_items);
+    ++clk.launches;
+    if (cub::DeviceRadixSort::SortPairsDescending(sort_tmp, sort_bytes, iw, keys, ids, order,
+                                                  int(n_items), 0, 64, s) != cudaSuccess)
+        return LOGAN_ECUDA;
+    cudaMemsetAsync(next, 0, 3 * sizeof(unsigned int), s);
     cudaMemsetAsync(ad_rlo, 0, sizeof(int32_t) * std::max<uint64_t>(total_ads, 1), s);
     cudaMemsetAsync(ad_word, 0, sizeof(uint64_t) * std::max<uint64_t>(total_ads, 1), s);
     if (clk.dcells) cudaMemsetAsync(clk.dcells, 0, sizeof(unsigned long long), s);
@@ -516,15 +570,25 @@ int run_traceback(int num_sms, const ExtensionViews& v, const logan_seed_t* seed
     t.ad_word = ad_word;
     t.n_words = total_words;
     t.cells = clk.dcells;
+    t.order = order;
+    t.next = next;
     clk.mark(TbClock::REC_START, s);
-    k_tb_record_warp<<<wgrid, kTbThreads, 0, s>>>(t);
-    k_tb_record_block<<<grid, kTbThreads, 0, s>>>(t);
+    // the block sweep of the items wide from the start runs beside the warp
+    // sweep (it holds a few SMs for long, the warp sweep fills the rest); the
+    // block sweep of the items that outgrew a warp's ring follows both
+    if (cudaEventRecord(S.fork, s) != cudaSuccess || cudaStreamWaitEvent(S.aux, S.fork, 0) != cudaSuccess)
+        return LOGAN_ECUDA;
+    k_tb_record_block<<<grid, kTbThreads, 0, s>>>(t, TB_WARP_WIDE, 1);
+    k_tb_record_warp<<<wgrid, kTbThreads, 0, S.aux>>>(t);
+    if (cudaEventRecord(S.join, S.aux) != cudaSuccess || cudaStreamWaitEvent(s, S.join, 0) != cudaSuccess)
+        return LOGAN_ECUDA;
+    k_tb_record_block<<<grid, kTbThreads, 0, s>>>(t, TB_OUTGREW, 2);
     clk.mark(TbClock::REC_END, s);
     k_tb_walk<<<(n_items + 127) / 128, 128, 0, s>>>(t, sd, n_pairs, op_start, ops, side_n);
     k_tb_join<<<(n_pairs + 127) / 128, 128, 0, s>>>(tinfo, sd, n_pairs, op_start, ops, side_n,
                                                     op_count);
     clk.mark(TbClock::END, s);
-    clk.launches += 4;
+    clk.launches += 5;
     clk.words = total_words;
     if (cudaStreamSynchronize(s) != cudaSuccess || cudaGetLastError() != cudaSuccess)
         return LOGAN_ECUDA;

@@ -135,8 +135,10 @@ def test_timing_stats(ctx):
     res = logan.results_to_numpy(ctx.extend(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs))
     assert 0 < st["record_cells"] <= int(res["cells"].sum())
     assert st["code_words"] >= st["record_cells"] // 16
-    # the pipeline's launches + prepare, two recording sweeps, walk, join
-    assert st["launches"] == ext_launches + 5
+    # the pipeline's launches + prepare, the item order's ids, three
+    # recording sweeps (blocks for the wide items beside the warps, blocks
+    # for the items that outgrew a warp), walk, join
+    assert st["launches"] == ext_launches + 7
 
 
 @pytest.mark.parametrize("opt,val", [("OPT_GRAPHS", 1), ("OPT_CONCURRENT", 0),
