@@ -260,8 +260,10 @@ typedef struct {
  * in (a, b, o) order, written to out (device, up to `capacity`); *n_found
  * (host) receives the number found (possibly above capacity).  1 <= k <= 31,
  * 2 <= min_freq <= max_freq <= 1024, min_shared >= 1.  Temporary memory is
- * taken from the device's stream-ordered pool (cudaMallocAsync) and returned
- * before the call ends; the call synchronises `stream`.  Returns
+ * taken stream-ordered from the context's own memory pool and freed before
+ * the call ends; the pool keeps it mapped for the next call until
+ * logan_ctx_destroy (the device's default pool if the context's cannot be
+ * created).  The call synchronises `stream`.  Returns
  * LOGAN_EINVAL for invalid arguments, LOGAN_ENOMEM when a temporary buffer
  * cannot be had, LOGAN_ECUDA on a CUDA failure. */
 int logan_overlap_candidates(logan_ctx_t *ctx, const logan_seqs_t *reads, int k,
@@ -323,8 +325,10 @@ int logan_overlap_keep(logan_ctx_t *ctx, const logan_result_t *results,
  * memory up to 2048 rows, else in a device-memory ring); one thread per
  * extension walks back.  The codes take about cells / 16 words of device
  * memory -- meant for the pairs a caller keeps, not whole raw batches.
- * Temporary memory comes from the stream-ordered pool (cudaMallocAsync); the
- * call synchronises `stream`.  With LOGAN_OPT_TIMING on, the call records
+ * Temporary memory comes stream-ordered from the context's own memory pool,
+ * as for logan_overlap_candidates; the call synchronises `stream` (the
+ * sweeps run on `stream` and on a second stream the call creates and joins).
+ * With LOGAN_OPT_TIMING on, the call records
  * CUDA events around its passes (logan_traceback_last_stats). */
 int logan_traceback_batch(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                           const logan_seqs_t *seqsB, const logan_seed_t *seeds,

@@ -97,6 +97,8 @@ struct logan_ctx {
     uint64_t use_clock = 0;
     // the last timed alignment-path call
     TracebackTiming tb_timing;
+    // scratch of the overlap and alignment-path calls (created on first use)
+    cudaMemPool_t scratch_pool = nullptr;
 };
 
 
@@ -160,6 +162,26 @@ Layout make_layout(const logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t
 }  // namespace
 
 TracebackTiming* logan::ctx_traceback_timing(logan_ctx_t* c) { return &c->tb_timing; }
+
+cudaMemPool_t logan::ctx_scratch_pool(logan_ctx_t* c) {
+    if (!c->scratch_pool) {
+        cudaMemPoolProps props{};
+        props.allocType = cudaMemAllocationTypePinned;
+        props.location.type = cudaMemLocationTypeDevice;
+        props.location.id = c->device;
+        cudaMemPool_t p = nullptr;
+        if (cudaMemPoolCreate(&p, &props) != cudaSuccess) return nullptr;
+        // keep freed scratch mapped between calls: re-mapping gigabytes on
+        // every call cost more than the seeding kernels themselves
+        uint64_t keep = ~uint64_t(0);
+        if (cudaMemPoolSetAttribute(p, cudaMemPoolAttrReleaseThreshold, &keep) != cudaSuccess) {
+            cudaMemPoolDestroy(p);
+            return nullptr;
+        }
+        c->scratch_pool = p;
+    }
+    return c->scratch_pool;
+}
 
 void logan::extension_views(const logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
                             uint32_t n_pairs, const void* ws, ExtensionViews* v) {
@@ -698,6 +720,7 @@ int logan_ctx_create(logan_ctx_t** out, int device, const char* autotune_json) {
 void logan_ctx_destroy(logan_ctx_t* c) {
     if (!c) return;
     DeviceGuard g(c->device);
+    if (c->scratch_pool) cudaMemPoolDestroy(c->scratch_pool);  // (its memory goes back now)
     for (auto& ge : c->graphs)
         if (ge.exec) cudaGraphExecDestroy(ge.exec);
     for (auto& a : c->aux) {

@@ -1,5 +1,5 @@
-// What the alignment-path call (traceback.cu) needs from the context and
-// from a finished logan_extend_batch, both defined in api.cu.
+// What the alignment-path and overlap calls (traceback.cu, overlap.cu) need
+// from the context and from a finished logan_extend_batch, defined in api.cu.
 #pragma once
 
 #include "internal.h"
@@ -15,6 +15,12 @@ struct TracebackTiming {
 
 // the context's record; never null for a valid context
 TracebackTiming* ctx_traceback_timing(logan_ctx_t* c);
+
+// The context's pool for the scratch of the overlap and alignment-path
+// calls: freed scratch stays mapped until the context is destroyed, so
+// repeated calls do not map gigabytes again.  Null if it cannot be created
+// (the callers then use the device's default pool).
+cudaMemPool_t ctx_scratch_pool(logan_ctx_t* c);
 
 // Device views into the workspace of a finished logan_extend_batch call
 // with the same pools and pair count: the 2-bit words of both pools, the

@@ -22,6 +22,7 @@
 #include <cstdint>
 #include <vector>
 
+#include "ctx_ext.h"
 #include "internal.h"
 
 #include "../../include/logan.h"
@@ -229,13 +230,16 @@ __global__ void k_overlap_keep(const logan_result_t* __restrict__ res,
 // stream-ordered scratch that frees itself
 struct Scratch {
     cudaStream_t s;
+    cudaMemPool_t pool;  // the context's scratch pool (null: the default one)
     std::vector<void*> ptrs;
     bool ok = true;
-    explicit Scratch(cudaStream_t st) : s(st) {}
+    Scratch(cudaStream_t st, cudaMemPool_t p) : s(st), pool(p) {}
     template <typename T>
     T* get(size_t n) {
         void* p = nullptr;
-        if (!ok || cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(T), s) != cudaSuccess) {
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        if (!ok || (pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s)
+                         : cudaMallocAsync(&p, bytes, s)) != cudaSuccess) {
             ok = false;
             return nullptr;
         }
@@ -297,7 +301,7 @@ extern "C" int logan_overlap_candidates(logan_ctx_t* ctx, const logan_seqs_t* re
     const uint32_t* w = static_cast<const uint32_t*>(reads->bases);
     int rc = LOGAN_OK;
     {
-        Scratch sc(s);
+        Scratch sc(s, ctx_scratch_pool(ctx));
         // 1. k-mer occurrences, (read, pos) order: first[r] = k-mers of
         // reads below r, first[R] = all of them
         uint64_t* cnt = sc.get<uint64_t>(R + 1);
@@ -453,7 +457,7 @@ extern "C" int logan_overlap_pool(logan_ctx_t* ctx, const logan_seqs_t* reads,
     if (words_capacity < need) return LOGAN_ENOMEM;
     int rc = LOGAN_OK;
     {
-        Scratch sc(s);
+        Scratch sc(s, ctx_scratch_pool(ctx));
         uint64_t* wfd = sc.get<uint64_t>(R);
         if (!sc.ok) return LOGAN_ENOMEM;
         if (R) cudaMemcpyAsync(wfd, wf.data(), sizeof(uint64_t) * R, cudaMemcpyHostToDevice, s);

@@ -419,12 +419,13 @@ __global__ void k_tb_join(const TbItem* __restrict__ info, const uint32_t* __res
 
 struct TbScratch {
     cudaStream_t s;
+    cudaMemPool_t pool;  // the context's scratch pool (null: the default one)
     std::vector<void*> ptrs;
     bool ok = true;
     // a second stream and its fork / join events, for the concurrent sweeps
     cudaStream_t aux = nullptr;
     cudaEvent_t fork = nullptr, join = nullptr;
-    explicit TbScratch(cudaStream_t st) : s(st) {
+    TbScratch(cudaStream_t st, cudaMemPool_t p) : s(st), pool(p) {
         ok = cudaStreamCreateWithFlags(&aux, cudaStreamNonBlocking) == cudaSuccess &&
              cudaEventCreateWithFlags(&fork, cudaEventDisableTiming) == cudaSuccess &&
              cudaEventCreateWithFlags(&join, cudaEventDisableTiming) == cudaSuccess;
@@ -432,7 +433,9 @@ struct TbScratch {
     template <typename T>
     T* get(size_t n) {
         void* p = nullptr;
-        if (!ok || cudaMallocAsync(&p, std::max<size_t>(n, 1) * sizeof(T), s) != cudaSuccess) {
+        const size_t bytes = std::max<size_t>(n, 1) * sizeof(T);
+        if (!ok || (pool ? cudaMallocFromPoolAsync(&p, bytes, pool, s)
+                         : cudaMallocAsync(&p, bytes, s)) != cudaSuccess) {
             ok = false;
             return nullptr;
         }
@@ -630,7 +633,7 @@ extern "C" int logan_traceback_batch(logan_ctx_t* ctx, const logan_seqs_t* A,
     int rc = LOGAN_OK;
     {
         TbClock clk(timing != 0);
-        TbScratch S(s);
+        TbScratch S(s, ctx_scratch_pool(ctx));
         size_t ws_bytes = 0;
         rc = logan_workspace_size(ctx, A, B, n_pairs, &ws_bytes);
         char* ws = rc == LOGAN_OK ? S.get<char>(ws_bytes) : nullptr;
