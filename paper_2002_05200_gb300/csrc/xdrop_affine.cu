@@ -309,7 +309,6 @@ __global__ void __launch_bounds__(128, 4) k_affine(KernelArgs ka, int go, int ge
     u.bpre = u.aw = u.bw = 0u;
     u.c32 = 0u;
     bool exhausted = false;
-    bool first_wave = true;  // the warp's first pop takes static slots
     for (;;) {
         u.cells += u.c32;
         u.c32 = 0u;
@@ -322,11 +321,17 @@ __global__ void __launch_bounds__(128, 4) k_affine(KernelArgs ka, int go, int ge
             uint32_t id = 0xffffffffu;
             const uint32_t want = __ballot_sync(FULL, need && gl == 0);
             if (want) {
+                const int leader = __ffs(want) - 1;
                 // levels run one after another, so a level's queue (its
                 // binned items, then those escalated into it) is complete
-                unsigned int limit = 0u;
-                const unsigned int slot = pop_unit_slot<G>(ka.counters, level, PHASE_WHOLE, want,
-                                                           lane, unit, first_wave, limit);
+                unsigned int first = 0u, limit = 0u;
+                if (lane == leader) {
+                    first = atomicAdd(&ka.counters->head[level], unsigned(__popc(want)));
+                    limit = ka.counters->tail[level];
+                }
+                first = __shfl_sync(FULL, first, leader);
+                limit = __shfl_sync(FULL, limit, leader);
+                const unsigned int slot = first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
                 if (need && slot < limit) id = q[slot];
             }
             if (need) {
