@@ -273,9 +273,11 @@ class Context:
         return list(arr)
 
     def autotune(self, A: DevicePool, B: DevicePool, seeds, match=1, mismatch=-1, gap=-1, X=50,
-                 X_per_pair=None, reps: int = 2, save: Optional[str] = None):
+                 X_per_pair=None, reps: int = 2, save: Optional[str] = None, stream=None):
         """Times every start level per X class on this sample batch and keeps
-        the fastest in the context's table; returns (table, ms[class][level])."""
+        the fastest in the context's table; returns (table, ms[class][level]).
+        Runs on `stream` (a torch stream; default the current one -- the legacy
+        default stream cannot be captured, so graphs need another)."""
         import torch
         n = int(seeds.shape[0])
         ws = self.workspace(A, B, n)
@@ -283,7 +285,8 @@ class Context:
         nl = num_levels()
         ms = (ctypes.c_float * (X_CLASSES * nl))()
         ca, cb = A.c(), B.c()
-        stream = torch.cuda.current_stream(self.device)
+        if stream is None:
+            stream = torch.cuda.current_stream(self.device)
         _check(lib().logan_autotune(self._h, ctypes.byref(ca), ctypes.byref(cb), seeds.data_ptr(),
                                     n, match, mismatch, gap, X,
                                     X_per_pair.data_ptr() if X_per_pair is not None else None,
