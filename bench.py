@@ -1007,8 +1007,7 @@ def main():
         args.autotune = 1 if args.workload in ("uneven_batch", "uniform_pairs") else 0
     stream = torch.cuda.Stream()
     if args.autotune:
-        # as the timed steps run: graph replay on the bench's stream
-        ctx.set_option(logan.OPT_GRAPHS, 1)
+        # as the timed steps run: direct launches on the bench's stream
         table, _ = ctx.autotune(A, B, S, b.match, b.mismatch, b.gap, b.X, Xs, reps=2,
                                 stream=stream)
         torch.cuda.synchronize()
@@ -1076,13 +1075,14 @@ def main():
     if args.traceback:
         return traceback_main(args, b, ctx, stream, rank, world, local, packed)
 
-    # persistent form.  The timed steps replay the call's captured launch
-    # sequence (LOGAN_OPT_GRAPHS; the warm-up captures it), as a caller
-    # running the same batch shape again would; the per-level device times
-    # come from as many further calls with per-level events (LOGAN_OPT_TIMING,
-    # which launches directly), right after the timed region
+    # persistent form.  The timed steps launch directly, with the context's
+    # default options (no graphs, no per-level events: graph replay helped a
+    # batch with one start level but made the multi-level uneven batch's
+    # steps erratic); the per-level device times come from as many further
+    # calls with per-level events (LOGAN_OPT_TIMING), right after the timed
+    # region
     ctx.set_option(logan.OPT_TIMING, 0)
-    ctx.set_option(logan.OPT_GRAPHS, 1)
+    ctx.set_option(logan.OPT_GRAPHS, 0)
     with ClockSampler(local) as clk:
         ms = timed(step, args.steps, args.warmup)
     res = logan.results_to_numpy(out)
@@ -1139,7 +1139,7 @@ def main():
             "cells_per_step": tot_cells,
             "levels": {"ms": [round(float(v), 4) for v in level_ms],
                        "items": last["items"], "cells": last["cells"]}}
-    line["launch"] = ("timed steps replay the call's CUDA graph (LOGAN_OPT_GRAPHS); per-level "
+    line["launch"] = ("timed steps launch directly (no graphs, no per-level events); per-level "
                       "times from as many calls with per-level events after the timed region")
     if tuned is not None:
         line["autotuned"] = tuned

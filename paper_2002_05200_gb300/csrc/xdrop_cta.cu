@@ -1,5 +1,7 @@
 // X-drop extension with a multi-warp unit per extension (window level 6:
 // 128 threads x 16 rows, level 7: 512 threads x 8 rows, in registers).
+// Level 6 runs here in its 32-bit form; when a call's scores fit 16 bits it
+// runs packed in one warp instead (xdrop_group16.cu).
 //
 // Same cell update as the G-lane kernels (paper Sec. III-A recurrence and
 // X-drop rule, Algorithm 2), with the anti-diagonal split across warps as in

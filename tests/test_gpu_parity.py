@@ -395,3 +395,20 @@ def test_packed_wide_bands_through_levels_5_6_7(ctx):
     assert st["packed_levels"] & (1 << 5) and st["packed_levels"] & (1 << 6), st["packed_levels"]
     assert st["items"][6] > 0 and st["items"][7] > 0, st["items"]
     assert_same(g, ref, "free gaps, levels 5-7")
+
+
+@pytest.mark.parametrize("level", [5, 6])
+@pytest.mark.parametrize("scheme", [(2, -3, -5, 60), (1, -2, -1, 120), (3, -1, -4, 40)])
+def test_two_virtual_lanes_other_scoring(ctx, level, scheme):
+    # the packed forms with two 32-row virtual lanes per lane (1024 and 2048
+    # rows) under other scoring schemes and X, started directly
+    match, mismatch, gap, X = scheme
+    b = synth.lognormal_batch(n_pairs=150, median=5000, lo=1000, hi=12_000, seed=41, X=X)
+    b.match, b.mismatch, b.gap = match, mismatch, gap
+    ref = run_oracle(b)
+    ctx.set_option(logan.OPT_FORCE_LEVEL, level)
+    ctx.set_option(logan.OPT_LONG_ITEM, -1)
+    ctx.set_option(logan.OPT_TIMING, 1)
+    g = run_gpu(ctx, b, packed2bit=True)
+    assert ctx.last_stats()["packed_levels"] & (1 << level)
+    assert_same(g, ref, f"level {level}, scheme {scheme}")
