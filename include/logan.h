@@ -531,13 +531,14 @@ int logan_get_escalation(const logan_ctx_t *ctx, int8_t *next, int n);
  * First, the start level of every X class present in the sample batch: one
  * pass of coordinate descent over the classes, each trying every level on
  * the whole sample with the other classes at their current choice; a level
- * replaces the class's current one only when the batch ran faster with it.
+ * replaces the class's current one only when the batch ran at least 3 %
+ * faster with it (step times vary by a few per cent between calls).
  * With the table chosen, the
  * whole sample runs for the two unit forms of each level -- packed 16-bit
  * or 32-bit (LOGAN_OPT_PACKED16 1 / 0) -- crossed with the one-warp rule for
  * small batches (LOGAN_OPT_LONG_ITEM -2 automatic / -1 several extensions
- * per warp always), and the fastest pair stays in the context (read back
- * with logan_get_option).
+ * per warp always), and the fastest pair replaces the context's (read back
+ * with logan_get_option) when it ran at least 3 % faster.
  * Arguments as logan_extend_batch; synchronous (it waits for every run and
  * copies X_per_pair to the host).  ms_table (nullable, host float
  * [LOGAN_X_CLASSES * logan_num_levels()]) receives the first stage's

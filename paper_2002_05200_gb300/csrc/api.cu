@@ -944,14 +944,16 @@ int logan_autotune(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
     for (int k = 0; k < kXClasses; ++k) chosen[k] = save_table.lv[k];
     if (ms_table)
         for (int k = 0; k < kXClasses * kNumLevels; ++k) ms_table[k] = -1.f;
+    // A candidate replaces the current choice only when it ran at least 3 %
+    // faster: step times of a batch vary by a few per cent between calls,
+    // and a choice made on that noise can cost far more on the next call.
+    constexpr float kGain = 0.97f;
     // the start level of each X class present: one pass of coordinate
     // descent on the whole sample -- every level for one class, the other
-    // classes at their current choice -- so that a level replaces a class's
-    // current one (itself a candidate) only when the whole batch ran faster
-    // with it
+    // classes at their current choice
     for (int cls = 0; cls < kXClasses && rc == LOGAN_OK; ++cls) {
         if (!present[cls]) continue;
-        float best_ms = 0.f;
+        float best_ms = 0.f, cur_ms = -1.f;
         int best_level = -1;
         for (int lvl = 0; lvl <= maxl && rc == LOGAN_OK; ++lvl) {
             int8_t trial[kXClasses];
@@ -962,12 +964,14 @@ int logan_autotune(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
             if (rc == LOGAN_OK) time_call(&t);
             if (rc != LOGAN_OK) break;
             if (ms_table) ms_table[cls * kNumLevels + lvl] = t;
+            if (lvl == chosen[cls]) cur_ms = t;
             if (best_level < 0 || t < best_ms) {
                 best_ms = t;
                 best_level = lvl;
             }
         }
-        if (best_level >= 0) chosen[cls] = int8_t(best_level);
+        if (best_level >= 0 && (cur_ms < 0.f || best_ms < kGain * cur_ms))
+            chosen[cls] = int8_t(best_level);
     }
     c->table = save_table;
     if (rc == LOGAN_OK) rc = set_table(c, chosen, kXClasses);
@@ -975,20 +979,23 @@ int logan_autotune(logan_ctx_t* c, const logan_seqs_t* A, const logan_seqs_t* B,
     // with the one-warp rule
     if (rc == LOGAN_OK) {
         const int64_t forms[4][2] = {{1, -2}, {1, -1}, {0, -2}, {0, -1}};
-        float best_ms = -1.f;
+        float best_ms = -1.f, cur_ms = -1.f;
         int best_form = -1;
         for (int f = 0; f < 4 && rc == LOGAN_OK; ++f) {
             c->packed16 = forms[f][0];
             c->long_item = forms[f][1];
             float t = -1.f;
             time_call(&t);
-            if (rc == LOGAN_OK && (best_form < 0 || t < best_ms)) {
+            if (rc != LOGAN_OK) break;
+            if (forms[f][0] == save_packed && forms[f][1] == save_long) cur_ms = t;
+            if (best_form < 0 || t < best_ms) {
                 best_ms = t;
                 best_form = f;
             }
         }
-        c->packed16 = best_form >= 0 ? forms[best_form][0] : save_packed;
-        c->long_item = best_form >= 0 ? forms[best_form][1] : save_long;
+        const bool take = best_form >= 0 && (cur_ms < 0.f || best_ms < kGain * cur_ms);
+        c->packed16 = take ? forms[best_form][0] : save_packed;
+        c->long_item = take ? forms[best_form][1] : save_long;
     } else {
         c->packed16 = save_packed;
         c->long_item = save_long;

@@ -198,7 +198,11 @@ def test_autotune_table_and_roundtrip(ctx, tmp_path):
     present = {x_class(int(x)) for x in b.Xs}
     for c in range(logan.X_CLASSES):
         if c in present:
-            assert all(t > 0 for t in ms[c]) and table[c] == int(np.argmin(ms[c]))
+            # the fastest level, or the previous choice when no level beat
+            # it by 3 %
+            assert all(t > 0 for t in ms[c])
+            assert table[c] == int(np.argmin(ms[c])) or (
+                table[c] == before[c] and min(ms[c]) >= 0.97 * ms[c][before[c]] - 1e-6)
         else:
             assert all(t == -1 for t in ms[c]) and table[c] == before[c]
     # results with the tuned table are still exact
