@@ -414,6 +414,7 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   LOGAN_OPT_CONCURRENT    concurrent start levels (below)
  *   LOGAN_OPT_LONG_ITEM     latency forms for long items (below)
  *   LOGAN_OPT_PACKED16      packed 16-bit level kernels (below)
+ *   LOGAN_OPT_AFFINE_PACKED which affine levels ran packed (read-only)
  */
 #define LOGAN_OPT_GRAPHS 1
 #define LOGAN_OPT_TIMING 2
@@ -455,7 +456,15 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                                     the start-level table when X is per pair
                                     or a start level is forced); otherwise,
                                     or with 0, the 32-bit form.  Results are
-                                    identical either way. */
+                                    identical either way.  The affine call's
+                                    windows of 128, 256 and 512 rows follow
+                                    the same option with |gap_open| +
+                                    |gap_extend| for |gap| and 2*|gap_extend|
+                                    in the second bound. */
+#define LOGAN_OPT_AFFINE_PACKED 12 /* read-only: bit l set when affine window
+                                    level l (64, 128, 256, 512 rows) ran in
+                                    its packed 16-bit form in the context's
+                                    last logan_extend_batch_affine call */
 int logan_set_option(logan_ctx_t *ctx, int option, int64_t value);
 int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
 

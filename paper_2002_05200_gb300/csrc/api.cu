@@ -65,6 +65,8 @@ struct logan_ctx {
     int blocks_per_sm[kNumLevels] = {};
     int twin_blocks_per_sm[kTwinLevels] = {};
     int affine_blocks_per_sm[4] = {};
+    int affine16_blocks_per_sm[4] = {};
+    uint32_t affine_packed_last = 0u;  // bit l: affine level l ran packed in the last call
     // LOGAN_OPT_LONG_ITEM: m + n from which items of levels < kTwinLevels
     // take the latency form; -1 never, -2 automatic
     int64_t long_item = -2;
@@ -317,6 +319,39 @@ uint32_t packed16_levels(const logan_ctx* c, Scoring sc, int32_t X, const int32_
     return mask;
 }
 
+// Affine levels that run in their packed 16-bit form in this call: those
+// with a packed kernel, when
+//   128 * (Xmax + 2*max(match,0) + |go| + |ge| + 2) + 31 <= 32767  and
+//   128 * (|mismatch| + |go| + 2*|ge| + 2*max(match,0) + 2) <= 16383,
+// Xmax the scalar X, or with per-pair X the upper bound of every X class
+// whose start level is at or below the level.  These bounds keep every
+// 16-bit half inside [0, 65536) through the kernel's additions
+// (xdrop_affine16.cu).
+uint32_t affine16_levels(const logan_ctx* c, Scoring sc, int go, int ge, int32_t X,
+                         const int32_t* Xs, const LevelTable& tab) {
+    if (!c->packed16) return 0u;
+    static const int64_t upper[kXClasses] = {15, 35, 75, 150, 300, 700, 2000, int64_t(1) << 29};
+    const int64_t mp = std::max<int64_t>(sc.match, 0);
+    const int64_t am = sc.mismatch < 0 ? -int64_t(sc.mismatch) : sc.mismatch;
+    const int64_t ao = -int64_t(go), ae = -int64_t(ge);
+    uint32_t mask = 0u;
+    for (int l = 0; l < affine_levels(); ++l) {
+        if (!affine16_level(l)) continue;
+        int64_t xmax = 0;
+        if (!Xs) {
+            xmax = X;
+        } else {
+            for (int k = 0; k < kXClasses; ++k)
+                if (tab.lv[k] <= l) xmax = std::max(xmax, upper[k]);
+        }
+        constexpr int64_t S = 128;  // score scale of the packed keys
+        if (S * (xmax + 2 * mp + ao + ae + 2) + 31 <= 32767 &&
+            S * (am + ao + 2 * ae + 2 * mp + 2) <= 16383)
+            mask |= 1u << l;
+    }
+    return mask;
+}
+
 // The whole pipeline on `s` (no synchronisation).  plain != 0: one-launch
 // form at c->plain_level, in input order.
 // aff != nullptr: affine gaps (gap_open, gap_extend), through the affine
@@ -423,12 +458,20 @@ int run_pipeline(logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t* B,
     if (aff) {
         // affine levels, narrowest first (each receives the bands that
         // outgrew the previous one), then the rejected items, then combine
+        const uint32_t apacked = affine16_levels(c, sc, aff->open, aff->extend, X, Xs, tab);
         for (int l = 0; l < affine_levels(); ++l) {
-            const int grid = c->num_sms * std::max(1, c->affine_blocks_per_sm[l]);
-            if (launch_affine_level(l, ka, aff->open, aff->extend, grid, s) != cudaSuccess)
-                return LOGAN_ECUDA;
+            cudaError_t le;
+            if ((apacked >> l) & 1u) {
+                const int grid = c->num_sms * std::max(1, c->affine16_blocks_per_sm[l]);
+                le = launch_affine16_level(l, ka, aff->open, aff->extend, affine_levels(), grid, s);
+            } else {
+                const int grid = c->num_sms * std::max(1, c->affine_blocks_per_sm[l]);
+                le = launch_affine_level(l, ka, aff->open, aff->extend, grid, s);
+            }
+            if (le != cudaSuccess) return LOGAN_ECUDA;
             ++launches;
         }
+        c->affine_packed_last = apacked;
         if (launch_affine_ring(ka, kWarpLevels, aff->open, aff->extend, int(L.ring_slots),
                                s) != cudaSuccess ||
             launch_combine(seeds, info, ext, n_pairs, out, s) != cudaSuccess)
@@ -694,7 +737,10 @@ int logan_ctx_create(logan_ctx_t** out, int device, const char* autotune_json) {
     for (int l = 0; l < kNumLevels; ++l)
         c->packed_blocks_per_sm[l] = packed_level(l) ? packed_level_blocks_per_sm(l) : 0;
     for (int l = 0; l < kTwinLevels; ++l) c->twin_blocks_per_sm[l] = twin_blocks_per_sm(l);
-    for (int l = 0; l < affine_levels(); ++l) c->affine_blocks_per_sm[l] = affine_blocks_per_sm(l);
+    for (int l = 0; l < affine_levels(); ++l) {
+        c->affine_blocks_per_sm[l] = affine_blocks_per_sm(l);
+        c->affine16_blocks_per_sm[l] = affine16_level(l) ? affine16_blocks_per_sm(l) : 0;
+    }
     for (auto& set : c->evs)
         for (auto& ev : set)
             if (cudaEventCreate(&ev) != cudaSuccess) {
@@ -836,6 +882,7 @@ int logan_get_option(const logan_ctx_t* c, int option, int64_t* v) {
         case LOGAN_OPT_CONCURRENT: *v = c->concurrent; return LOGAN_OK;
         case LOGAN_OPT_LONG_ITEM: *v = c->long_item; return LOGAN_OK;
         case LOGAN_OPT_PACKED16: *v = c->packed16; return LOGAN_OK;
+        case LOGAN_OPT_AFFINE_PACKED: *v = c->affine_packed_last; return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }

@@ -87,9 +87,14 @@ int affine_levels();
 int affine_blocks_per_sm(int level);
 cudaError_t launch_affine_level(int level, const KernelArgs& ka, int gap_open, int gap_extend,
                                 int grid, cudaStream_t s);
+// their packed 16-bit forms (xdrop_affine16.cu), for the levels that have one
+bool affine16_level(int level);
+cudaError_t launch_affine16_level(int level, const KernelArgs& ka, int gap_open, int gap_extend,
+                                  int n_levels, int grid, cudaStream_t s);
+int affine16_blocks_per_sm(int level);
 // bands that outgrow the affine windows, and X too large for their keys:
 // every entry of queue q continues in the device-memory ring kernel
-// (xdrop_matrix.cu) with half the workspace ring's width
+// (xdrop_matrix.cu) at the workspace ring's width
 cudaError_t launch_affine_ring(const KernelArgs& ka, int q, int go, int ge, int grid,
                                cudaStream_t s);
 

@@ -163,3 +163,41 @@ def test_lognormal_100k_every_pair(ctx):
     k = b.seeds["len"].astype(np.int64)
     assert np.array_equal(g["score"][ok].astype(np.int64),
                           (g["left"].astype(np.int64) + k * b.match + g["right"])[ok])
+
+
+@pytest.mark.parametrize("scheme", [(1, -1, -2, -1, 100), (2, -3, -5, -2, 60), (1, -1, 0, -1, 200),
+                                    (1, -2, -30, -10, 40)])
+def test_packed_levels_equal_32bit_and_oracle(ctx, scheme):
+    # the packed 16-bit windows (128, 256, 512 rows) and the 32-bit ones give
+    # the oracle's results; a call reports which levels ran packed
+    match, mismatch, go, ge, X = scheme
+    b = synth.lognormal_batch(n_pairs=300, median=6000, lo=1000, hi=20_000, seed=77, X=X)
+    b.match, b.mismatch = match, mismatch
+    ref = ref_affine(b, go, ge)
+    try:
+        ctx.set_option(logan.OPT_PACKED16, 1)
+        g16 = run_affine(ctx, b, go, ge, packed2bit=True)
+        packed = ctx.get_option(logan.OPT_AFFINE_PACKED)
+        ctx.set_option(logan.OPT_PACKED16, 0)
+        g32 = run_affine(ctx, b, go, ge, packed2bit=True)
+        assert ctx.get_option(logan.OPT_AFFINE_PACKED) == 0
+    finally:
+        ctx.set_option(logan.OPT_PACKED16, 1)
+    assert packed == 0b1110, packed  # levels 1-3 (128, 256, 512 rows)
+    assert_same(g16, ref, f"packed {scheme}")
+    assert_same(g32, ref, f"32-bit {scheme}")
+
+
+def test_packed_levels_per_pair_x_and_bounds(ctx):
+    # per-pair X up to 500: only the levels whose X classes fit stay packed;
+    # scores too large for 16 bits keep every level 32-bit
+    b = synth.uneven_batch(n_pairs=150, max_len=20_000, seed=78)
+    g = run_affine(ctx, b, -2, -1, packed2bit=True)
+    packed = ctx.get_option(logan.OPT_AFFINE_PACKED)
+    assert packed & 0b0010 and not packed & 0b1000, packed
+    assert_same(g, ref_affine(b, -2, -1), "uneven, per-pair X")
+    b2 = synth.lognormal_batch(n_pairs=60, seed=79, X=100)
+    b2.match, b2.mismatch = 300, -300
+    g2 = run_affine(ctx, b2, -300, -300, packed2bit=True)
+    assert ctx.get_option(logan.OPT_AFFINE_PACKED) == 0
+    assert_same(g2, ref_affine(b2, -300, -300), "large scores")
