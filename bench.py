@@ -48,10 +48,10 @@ METRIC = "X-drop GCUPS (computed cells), batched vs plain launch; serving p50/p9
 #             FMA pipe (IMAD, from sass__inst_executed_per_opcode), the rest
 #             going to the ALU pipe or to pipes that are not near a limit.
 # Reported only while the kernel's sources are the ones captured.
-PROFILED = {"level": 2, "bytes": 114.062848e6 + 8.978432e6, "items": 48_000,
-            "fma_share": 6174503468 / 20168436954,
+PROFILED = {"level": 2, "bytes": 114.171904e6 + 9.26592e6, "items": 48_000,
+            "fma_share": 6171644505 / 20159301634,
             "sources": ("xdrop_group16.cu", "packed16.cuh", "logan_dev.cuh", "internal.h"),
-            "sha1": "1d3816ad2c80f068c9664c4daaed39598bdbd460"}
+            "sha1": "018a8d6b1c9b48304bbd4acb8c1f2e36f6878139"}
 OPS_PER_CELL_AFFINE = 12  # Gotoh per cell: compare, diag add, E: 2 adds + max, F: 2 adds + max, 2 max, X-drop compare, select
 # The scope table's count for the linear recurrence, per cell: substitution
 # select, diag + substitution, max(up, left), + gap and max with the diagonal
