@@ -415,6 +415,7 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   LOGAN_OPT_LONG_ITEM     latency forms for long items (below)
  *   LOGAN_OPT_PACKED16      packed 16-bit level kernels (below)
  *   LOGAN_OPT_AFFINE_PACKED which affine levels ran packed (read-only)
+ *   LOGAN_OPT_MATRIX_PACKED which matrix windows ran packed (read-only)
  */
 #define LOGAN_OPT_GRAPHS 1
 #define LOGAN_OPT_TIMING 2
@@ -465,6 +466,11 @@ int logan_extend_batch_noalloc(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
                                     level l (64, 128, 256, 512 rows) ran in
                                     its packed 16-bit form in the context's
                                     last logan_extend_batch_affine call */
+#define LOGAN_OPT_MATRIX_PACKED 13 /* read-only: bit l set when the matrix
+                                    call's window l (64, 128, 256, 512 rows)
+                                    ran in its packed 16-bit form in the
+                                    context's last logan_extend_batch_matrix
+                                    call (scalar X only) */
 int logan_set_option(logan_ctx_t *ctx, int option, int64_t value);
 int logan_get_option(const logan_ctx_t *ctx, int option, int64_t *value);
 

@@ -67,6 +67,7 @@ struct logan_ctx {
     int affine_blocks_per_sm[4] = {};
     int affine16_blocks_per_sm[4] = {};
     uint32_t affine_packed_last = 0u;  // bit l: affine level l ran packed in the last call
+    uint32_t matrix_packed_last = 0u;  // bit l: matrix window l ran packed in the last call
     // LOGAN_OPT_LONG_ITEM: m + n from which items of levels < kTwinLevels
     // take the latency form; -1 never, -2 automatic
     int64_t long_item = -2;
@@ -164,6 +165,8 @@ Layout make_layout(const logan_ctx* c, const logan_seqs_t* A, const logan_seqs_t
 }  // namespace
 
 TracebackTiming* logan::ctx_traceback_timing(logan_ctx_t* c) { return &c->tb_timing; }
+
+void logan::ctx_set_matrix_packed(logan_ctx_t* c, uint32_t levels) { c->matrix_packed_last = levels; }
 
 cudaMemPool_t logan::ctx_scratch_pool(logan_ctx_t* c) {
     if (!c->scratch_pool) {
@@ -883,6 +886,7 @@ int logan_get_option(const logan_ctx_t* c, int option, int64_t* v) {
         case LOGAN_OPT_LONG_ITEM: *v = c->long_item; return LOGAN_OK;
         case LOGAN_OPT_PACKED16: *v = c->packed16; return LOGAN_OK;
         case LOGAN_OPT_AFFINE_PACKED: *v = c->affine_packed_last; return LOGAN_OK;
+        case LOGAN_OPT_MATRIX_PACKED: *v = c->matrix_packed_last; return LOGAN_OK;
         default: return LOGAN_EINVAL;
     }
 }

@@ -22,6 +22,10 @@ TracebackTiming* ctx_traceback_timing(logan_ctx_t* c);
 // (the callers then use the device's default pool).
 cudaMemPool_t ctx_scratch_pool(logan_ctx_t* c);
 
+// the matrix call's record of the windows that ran packed (read back with
+// LOGAN_OPT_MATRIX_PACKED)
+void ctx_set_matrix_packed(logan_ctx_t* c, uint32_t levels);
+
 // Device views into the workspace of a finished logan_extend_batch call
 // with the same pools and pair count: the 2-bit words of both pools, the
 // split items (two per pair, left first), every item's result (best cell,

@@ -31,14 +31,16 @@
 #include <algorithm>
 #include <climits>
 
+#include "ctx_ext.h"
 #include "internal.h"
+#include "packed16.cuh"
 #include "../../include/logan.h"
 
 namespace logan {
 
 namespace {
 
-constexpr uint32_t FULL = 0xffffffffu;
+// (FULL, the packed keys and reductions: packed16.cuh)
 constexpr int kMxThreads = 256;
 constexpr int kMxWarps = kMxThreads / 32;
 constexpr int NEGM = -(1 << 30);  // -inf of the absolute scores
@@ -93,6 +95,8 @@ struct MxArgs {
     int32_t* ring;  // per block: 6 * cap cells
     uint32_t cap;   // power of two
     int cells_level;  // counters->cells index credited with the cells
+    int sub_min;      // the table's smallest entry (packed windows)
+    int one;          // 1 at run time: additions as multiply-adds (FMA pipe)
 };
 
 template <bool BYTES>
@@ -579,6 +583,377 @@ int mx_level_blocks(int level) {
     return e == cudaSuccess ? std::max(1, n) : 1;
 }
 
+// ---- packed register windows: two rows per 32-bit register ----
+//
+// The packed affine windows (xdrop_affine16.cu) for letter codes: units of G
+// lanes x 32 rows, register h of a lane holding rows h and h + 16 as 16-bit
+// keys 32768 + 128*u + (31 - k) (DEAD = 16384), H on d-2 / d-1 / d in three
+// rotating arrays, E and F in place with the registers in descending order.
+// A lane keeps its rows' letters as 16-bit halves too: A16[h] = a' letters of
+// rows (h, h + 16), B16[h] = their b' letters, which move up one register per
+// anti-diagonal (register 0 takes the row below: a byte permute, plus one
+// shuffle from the lower lane).  The substitution of a pair of cells is
+// A16[h] * K + B16[h] (both table indices in one multiply-add) and two 16-bit
+// loads of the table, kept in shared memory as 128 (M[x][y] - min M): the
+// diagonal term is H(d-2) + 128 (min M + T_{d-2} - T_d) - 1 + that entry,
+// which the bounds below keep inside [0, 65536) with no carry between
+// halves.  The host runs a window packed only when
+//   128*(Xmax + 2*max(max M,0) + |go| + |ge| + 2) + 31 <= 32767   and
+//   128*(|min M| + |go| + 2*|ge| + 2*max(max M,0) + 2) <= 16383
+// (the packed affine windows' bounds with max M and min M for match and
+// mismatch); a band that outgrows a window restarts at the next.
+
+struct M16 {
+    int base, lo, hi, d;
+    int best, T, T1, T2;
+    int bi, bj;
+    int m, n, X;
+    unsigned long long cells;
+    uint32_t c32;  // cells of the current loop iteration, folded into cells at its top
+    int64_t apos, bpos;
+    int dir;
+    int q0;
+    uint32_t bpre;  // this lane's 4 prefetched b' letters: q0 + 4g ...
+    uint32_t item;
+    bool active, done, overflow;
+};
+
+// letters of rows (h, h+16), h < 16, of the 32 rows from stream index q
+// (row r: index q + r, or q - r for the b' stream read backwards), as halves
+template <bool BACK>
+__device__ __forceinline__ void m16_letters(const uint8_t* __restrict__ pool, int64_t pos, int dir,
+                                            int len, int64_t q, uint32_t (&L)[16]) {
+#pragma unroll
+    for (int h = 0; h < 16; ++h) {
+        const int64_t q0 = BACK ? q - h : q + h;
+        const int64_t q1 = BACK ? q - h - 16 : q + h + 16;
+        L[h] = mx_letter(pool, pos, dir, len, q0) | (mx_letter(pool, pos, dir, len, q1) << 16);
+    }
+}
+
+template <int G>
+__device__ __forceinline__ void m16_init(const MxArgs& a, M16& u, uint32_t id, int gl,
+                                         uint32_t (&H2)[16], uint32_t (&H1)[16], uint32_t (&E)[16],
+                                         uint32_t (&F)[16], uint32_t (&A16)[16], uint32_t (&B16)[16]) {
+    const Item it = a.items[id];
+    const uint8_t* pa = static_cast<const uint8_t*>(a.pa);
+    const uint8_t* pb = static_cast<const uint8_t*>(a.pb);
+    u.item = id;
+    u.apos = it.a_pos;
+    u.bpos = it.b_pos;
+    u.dir = (it.flags & ITEM_LEFT) ? -1 : 1;
+    u.m = int(it.m);
+    u.n = int(it.n);
+    u.X = it.X;
+    u.base = u.lo = u.hi = 0;
+    u.d = 1;
+    u.best = 0;
+    u.T = u.T1 = u.T2 = -it.X;
+    u.bi = u.bj = 0;
+    u.cells = 0ull;
+    u.q0 = 0;
+    u.bpre = mx_letters4(pb, u.bpos, u.dir, u.n, 4 * gl);
+#pragma unroll
+    for (int h = 0; h < 16; ++h) {
+        H2[h] = H1[h] = E[h] = F[h] = DEAD2;
+        B16[h] = 0u;
+    }
+    // S(0,0) = 0 relative to T_0 = -X, window row 0; it has no gap state
+    if (gl == 0) H1[0] = (DEAD2 & 0xffff0000u) | live_key(it.X, 0);
+    // row r needs a' index base + g*32 + r - 1
+    m16_letters<false>(pa, u.apos, u.dir, u.m, int64_t(gl) * 32 - 1, A16);
+    u.active = true;
+    u.done = false;
+    u.overflow = false;
+}
+
+// result, next window or the ring of a finished unit (leader lane)
+__device__ __forceinline__ void m16_finish(const MxArgs& a, const M16& u, int level, int gl) {
+    if (gl != 0) return;
+    if (u.overflow) {
+        const int nq = level + 1 < kMxLevels ? level + 1 : kMxRingQueue;
+        const unsigned int t = atomicAdd(&a.counters->tail[nq], 1u);
+        a.queues[size_t(nq) * a.qcap + t] = u.item;
+        return;
+    }
+    ExtRes r;
+    r.best = u.best;
+    r.bi = u.bi;
+    r.bj = u.bj;
+    r.status = 0;
+    r.cells = u.cells;
+    a.ext[u.item] = r;
+    atomicAdd(&a.counters->cells[level], u.cells);
+}
+
+// Loop top: slide by half-lanes so that the next three steps fit (a band that
+// cannot overflows), keep the b' prefetch covering them.
+template <int G>
+__device__ __forceinline__ void m16_prepare(const MxArgs& a, M16& u, int gl, uint32_t (&H2)[16],
+                                            uint32_t (&H1)[16], uint32_t (&E)[16],
+                                            uint32_t (&F)[16], uint32_t (&A16)[16],
+                                            uint32_t (&B16)[16]) {
+    constexpr int W = P16<G, 1>::W;
+    const uint8_t* pa = static_cast<const uint8_t*>(a.pa);
+    const uint8_t* pb = static_cast<const uint8_t*>(a.pb);
+    const int rlo = max(u.lo, u.d - u.n);
+    const int top = min(u.hi + 3, u.m);
+    const bool need = u.active && top >= u.base + W;
+    if (__any_sync(FULL, need)) {
+        const int s = need ? (rlo - 1 - u.base) / 16 : 0;
+        const bool ovf = need && (s <= 0 || top >= u.base + s * 16 + W);
+        const int sh = (need && !ovf) ? s : 0;  // half-lanes to drop
+        const int t = sh >> 1;
+        const bool odd = (sh & 1) != 0;
+        const bool lo_ok = 2 * gl + sh < 2 * G;
+        const bool hi_ok = 2 * gl + sh + 1 < 2 * G;
+        const uint32_t keep = (lo_ok ? 0x0000ffffu : 0u) | (hi_ok ? 0xffff0000u : 0u);
+        // keys: an odd shift moves rows k + 16 to k (code + 16) and the next
+        // lane's rows k to k + 16 (code - 16); letters move as they are
+        const uint32_t rebase = odd ? 16u - (16u << 16) : 0u;
+        auto slide = [&](uint32_t& r, bool key) {
+            uint32_t x = __shfl_down_sync(FULL, r, t, G);
+            const uint32_t y = __shfl_down_sync(FULL, r, t + 1, G);
+            if (odd) x = __byte_perm(x, y, 0x5432);
+            if (sh > 0) r = key ? (((x + rebase) & keep) | (DEAD2 & ~keep)) : x;
+        };
+#pragma unroll
+        for (int h = 0; h < 16; ++h) {
+            slide(H2[h], true);
+            slide(H1[h], true);
+            slide(E[h], true);
+            slide(F[h], true);
+            slide(A16[h], false);
+            slide(B16[h], false);
+        }
+        if (sh > 0) {
+            u.base += 16 * sh;
+            if (!(lo_ok && hi_ok)) {
+                // rows new to the window: letters from memory (b' as of d-1)
+                const int64_t i0 = int64_t(u.base) + int64_t(gl) * 32;
+                m16_letters<false>(pa, u.apos, u.dir, u.m, i0 - 1, A16);
+                m16_letters<true>(pb, u.bpos, u.dir, u.n, int64_t(u.d) - 2 - i0, B16);
+            }
+        }
+        if (ovf) {
+            u.active = false;
+            u.done = true;
+            u.overflow = true;
+        }
+    }
+    const int q = u.d - u.base - 1;  // the next three steps read q .. q+2
+    const bool refill = u.active && (q < u.q0 || q + 2 >= u.q0 + 4 * G);
+    if (__any_sync(FULL, refill)) {
+        if (refill) {
+            u.q0 = q;
+            u.bpre = mx_letters4(pb, u.bpos, u.dir, u.n, int64_t(q) + 4 * gl);
+        }
+    }
+}
+
+// One anti-diagonal of every unit of the warp (H2 = d-2, H1 = d-1, O = d;
+// E, F on d-1 replaced by d; B16 moves to d's letters).
+template <int G>
+__device__ __forceinline__ void m16_step(const MxArgs& a, const uint16_t* tab, M16& u, int gl,
+                                         int unit, const uint32_t (&H2)[16],
+                                         const uint32_t (&H1)[16], uint32_t (&O)[16],
+                                         uint32_t (&E)[16], uint32_t (&F)[16],
+                                         const uint32_t (&A16)[16], uint32_t (&B16)[16]) {
+    constexpr int W = P16<G, 1>::W;
+    const int rlo = max(u.lo, u.d - u.n);
+    const int rhi = min(u.hi + 1, u.m);
+    const bool run = u.active && rlo <= rhi;
+    // b' letters move up one row; window row 0 takes stream index d - base - 1
+    const int qq = u.d - u.base - 1 - u.q0;
+    const uint32_t pre = __shfl_sync(FULL, u.bpre, unit * G + ((qq >> 2) & (G - 1)));
+    const uint32_t front = (pre >> (8u * uint32_t(qq & 3))) & 0xffu;
+    uint32_t bb = __shfl_up_sync(FULL, B16[15], 1, G);
+    uint32_t b0 = __byte_perm(bb, B16[15], 0x5432);  // (lower lane's row 31, own row 15)
+    b0 = gl == 0 ? ((b0 & 0xffff0000u) | front) : b0;
+#pragma unroll
+    for (int h = 15; h >= 1; --h) B16[h] = B16[h - 1];
+    B16[0] = b0;
+    // the row below register 0: lower lane's row 31, own row 15; the lower
+    // lane's row 31 has code 0 where row 0 expects code 32: +32 on the low half
+    uint32_t xu = __shfl_up_sync(FULL, H1[15], 1, G);
+    uint32_t xd = __shfl_up_sync(FULL, H2[15], 1, G);
+    uint32_t xf = __shfl_up_sync(FULL, F[15], 1, G);
+    xu = gl == 0 ? DEAD2 : xu;
+    xd = gl == 0 ? DEAD2 : xd;
+    xf = gl == 0 ? DEAD2 : xf;
+    const uint32_t one = uint32_t(a.one);
+    const uint32_t U0 = __byte_perm(xu, H1[15], 0x5432) * one + 32u;
+    const uint32_t D0 = __byte_perm(xd, H2[15], 0x5432) * one + 32u;
+    const uint32_t F0 = __byte_perm(xf, F[15], 0x5432) * one + 32u;
+    const int gE = (a.ge + u.T1 - u.T) * KS;
+    const int gH = (a.go + a.ge + u.T1 - u.T) * KS;
+    const uint32_t GE = uint32_t(gE) * 0x10001u;
+    const uint32_t GH = uint32_t(gH) * 0x10001u;
+    const uint32_t GEu = uint32_t(gE - 1) * 0x10001u;
+    const uint32_t GHu = uint32_t(gH - 1) * 0x10001u;
+    const uint32_t SM = uint32_t((a.sub_min + u.T2 - u.T) * KS - 1) * 0x10001u;
+    const uint32_t K = uint32_t(a.K);
+    const int i0 = u.base + gl * 32;
+    const int k0 = __viaddmin_s32_relu(rlo, -i0, 32);
+    const int k1 = __viaddmin_s32_relu(rhi, 1 - i0, 32);
+    const uint32_t rb = __funnelshift_lc(~0u, 0u, k1) & ~__funnelshift_lc(~0u, 0u, k0);
+    uint32_t L = 0u;
+    uint32_t lk1 = 0u;
+#pragma unroll
+    for (int h = 15; h >= 0; --h) {  // descending: F[h-1] still holds d-1
+        const uint32_t hu = h ? H1[h - 1] : U0;
+        const uint32_t fu = h ? F[h - 1] : F0;
+        const uint32_t dg = h ? H2[h - 1] : D0;
+        const uint32_t e = __vimax3_u16x2(E[h] * one + GE, H1[h] * one + GH, 0u);
+        const uint32_t f = __vimax3_u16x2(fu * one + GEu, hu * one + GHu, 0u);
+        // both cells' table indices, a' letter * K + b' letter, in one
+        const uint32_t idx = A16[h] * K + B16[h];
+        const uint32_t sub = __byte_perm(uint32_t(tab[idx & 0xffffu]), uint32_t(tab[idx >> 16]),
+                                         0x5410);
+        const uint32_t t2 = sub * one + (dg * one + SM);
+        const uint32_t v = __vimax3_u16x2(t2, e, f);
+        const uint32_t x = v & (rb << (15 - h) & 0x80008000u);
+        const uint32_t mk = sign_mask16(x);  // 0xffff per live half
+        O[h] = (v & mk) | (DEAD2 & ~mk);
+        E[h] = (e & mk) | (DEAD2 & ~mk);
+        F[h] = (f & mk) | (DEAD2 & ~mk);
+        L |= mk & (0x10001u << h);
+    }
+#pragma unroll
+    for (int h = 0; h < 16; h += 2) lk1 = __vimax3_u16x2(lk1, O[h], O[h + 1]);
+    const uint32_t lkey = max(lk1 & 0xffffu, lk1 >> 16);
+    const uint32_t fkey = lkey >= LIVE ? (((lkey - LIVE) >> LOG2KS) << P16<G, 1>::LOG2W) |
+                                             uint32_t(W - 32 - gl * 32) + (lkey & 31u)
+                                       : 0u;
+    const int fr = __ffs(L) - 1, lr = 31 - __clz(L);
+    const uint32_t flw = L ? (uint32_t(W - (gl * 32 + fr)) | (uint32_t(gl * 32 + lr + 1) << 16)) : 0u;
+    const uint32_t wkey = unit_max_u32<G>(fkey);
+    const uint32_t fl = unit_max_u16x2<G>(flw);
+    u.c32 += run ? uint32_t(rhi - rlo + 1) : 0u;
+    const bool adv = run && fl != 0u;
+    const int umax = int(wkey >> P16<G, 1>::LOG2W);
+    const bool imp = adv && umax > u.X;  // S > best  <=>  S - T_d > X
+    const int r = W - 1 - int(wkey & uint32_t(W - 1));
+    const int best = imp ? u.T + umax : u.best;
+    u.bi = imp ? u.base + r : u.bi;
+    u.bj = imp ? u.d - (u.base + r) : u.bj;
+    u.best = best;
+    const int T = u.T, T1 = u.T1;
+    u.T2 = adv ? T1 : u.T2;
+    u.T1 = adv ? T : T1;
+    u.T = adv ? best - u.X : T;
+    u.lo = adv ? u.base + (W - int(fl & 0xffffu)) : u.lo;
+    u.hi = adv ? u.base + int(fl >> 16) - 1 : u.hi;
+    u.done = u.done || (u.active && !adv);
+    u.active = u.active && adv;
+    u.d += 1;
+}
+
+template <int G>
+__global__ void __launch_bounds__(128, 2) k_mx16(MxArgs a, int level) {
+    __shared__ uint16_t tab[kMaxK * kMaxK];
+    // 128 (M[x][y] - min M): 16-bit, non-negative under the host's bounds
+    for (int t = threadIdx.x; t < a.K * a.K; t += blockDim.x)
+        tab[t] = uint16_t((a.table[t] - a.sub_min) * KS);
+    __syncthreads();
+    const int lane = threadIdx.x & 31;
+    const int gl = lane % G, unit = lane / G;
+    const uint32_t* q = a.queues + size_t(level) * a.qcap;
+    uint32_t P0[16], P1[16], P2[16], E[16], F[16], A16[16], B16[16];
+#pragma unroll
+    for (int h = 0; h < 16; ++h) {
+        P0[h] = P1[h] = P2[h] = E[h] = F[h] = DEAD2;
+        A16[h] = B16[h] = 0u;
+    }
+    M16 u;
+    u.active = u.done = u.overflow = false;
+    u.item = 0u;
+    u.m = u.n = 0;
+    u.base = u.lo = u.hi = 0;
+    u.d = 1;
+    u.best = u.bi = u.bj = 0;
+    u.T = u.T1 = u.T2 = 0;
+    u.X = 0;
+    u.cells = 0ull;
+    u.c32 = 0u;
+    u.apos = u.bpos = 0;
+    u.dir = 1;
+    u.q0 = 0;
+    u.bpre = 0u;
+    bool exhausted = false;
+    for (;;) {
+        u.cells += u.c32;
+        u.c32 = 0u;
+        if (__any_sync(FULL, u.done || (!u.active && !exhausted))) {
+            if (u.done) {
+                m16_finish(a, u, level, gl);
+                u.done = false;
+            }
+            const bool need = !u.active && !exhausted;
+            uint32_t id = 0xffffffffu;
+            const uint32_t want = __ballot_sync(FULL, need && gl == 0);
+            if (want) {
+                const int leader = __ffs(want) - 1;
+                // levels run one after another, so a level's queue is complete
+                unsigned int first = 0u, limit = 0u;
+                if (lane == leader) {
+                    first = atomicAdd(&a.counters->head[level], unsigned(__popc(want)));
+                    limit = a.counters->tail[level];
+                }
+                first = __shfl_sync(FULL, first, leader);
+                limit = __shfl_sync(FULL, limit, leader);
+                const unsigned int slot = first + unsigned(__popc(want & ((1u << (unit * G)) - 1u)));
+                if (need && slot < limit) id = q[slot];
+            }
+            if (need) {
+                if (id != 0xffffffffu) m16_init<G>(a, u, id, gl, P0, P1, E, F, A16, B16);
+                else exhausted = true;
+            }
+        }
+        if (!__any_sync(FULL, u.active)) break;
+        m16_prepare<G>(a, u, gl, P0, P1, E, F, A16, B16);
+        m16_step<G>(a, tab, u, gl, unit, P0, P1, P2, E, F, A16, B16);
+        m16_step<G>(a, tab, u, gl, unit, P1, P2, P0, E, F, A16, B16);
+        m16_step<G>(a, tab, u, gl, unit, P2, P0, P1, E, F, A16, B16);
+    }
+}
+
+// matrix level -> G of its packed form (one 32-row lane; level 0, 64 rows,
+// has none)
+#define LOGAN_MX16_LEVELS(X) X(1, 4) X(2, 8) X(3, 16)
+
+bool mx16_level(int level) {
+    switch (level) {
+#define CASE(L, G) case L: return true;
+        LOGAN_MX16_LEVELS(CASE)
+#undef CASE
+        default: return false;
+    }
+}
+
+cudaError_t launch_mx16_level(int level, const MxArgs& a, int grid, cudaStream_t s) {
+    switch (level) {
+#define CASE(L, G) case L: k_mx16<G><<<grid, 128, 0, s>>>(a, L); break;
+        LOGAN_MX16_LEVELS(CASE)
+#undef CASE
+        default: return cudaErrorInvalidValue;
+    }
+    return cudaGetLastError();
+}
+
+int mx16_level_blocks(int level) {
+    int n = 0;
+    cudaError_t e = cudaErrorInvalidValue;
+    switch (level) {
+#define CASE(L, G) \
+    case L: e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, k_mx16<G>, 128, 0); break;
+        LOGAN_MX16_LEVELS(CASE)
+#undef CASE
+        default: break;
+    }
+    return e == cudaSuccess ? std::max(1, n) : 1;
+}
+
 // ---- the matrix call's own pre-processing ----
 
 // per sequence: 1 if a letter code is >= K
@@ -710,7 +1085,7 @@ MxLayout mx_layout(int num_sms, const logan_seqs_t* A, const logan_seqs_t* B, ui
 cudaError_t launch_affine_ring(const KernelArgs& ka, int q, int go, int ge, int grid,
                                cudaStream_t s) {
     if (grid <= 0) return cudaSuccess;
-    MxArgs a;
+    MxArgs a{};
     a.pa = ka.wa;
     a.pb = ka.wb;
     a.items = ka.items;
@@ -768,11 +1143,31 @@ extern "C" int logan_extend_batch_matrix(logan_ctx_t* ctx, const logan_seqs_t* s
         return LOGAN_EINVAL;
     if (X < 0 || X > kMaxX) return LOGAN_EINVAL;
     int64_t big = int64_t(-gap_open) - gap_extend;
+    int32_t sub_min = matrix[0], sub_max = matrix[0];
     for (int t = 0; t < K * K; ++t) {
         const int64_t v = matrix[t] < 0 ? -int64_t(matrix[t]) : matrix[t];
         if (v > kMaxParam) return LOGAN_EINVAL;
         big = std::max(big, v);
+        sub_min = std::min(sub_min, matrix[t]);
+        sub_max = std::max(sub_max, matrix[t]);
     }
+    // windows of 128-512 rows run packed (two 16-bit cells per register) when
+    // the scores provably fit (see the packed kernel); with per-pair X the
+    // call does not know the largest X, and keeps the 32-bit windows
+    uint32_t packed = 0u;
+    int64_t opt_packed = 1;
+    logan_get_option(ctx, LOGAN_OPT_PACKED16, &opt_packed);
+    if (opt_packed && !X_per_pair) {
+        const int64_t mp = std::max<int64_t>(sub_max, 0);
+        const int64_t am = sub_min < 0 ? -int64_t(sub_min) : sub_min;
+        const int64_t ao = -int64_t(gap_open), ae = -int64_t(gap_extend);
+        constexpr int64_t S = 128;  // score scale of the packed keys
+        if (S * (int64_t(X) + 2 * mp + ao + ae + 2) + 31 <= 32767 &&
+            S * (am + ao + 2 * ae + 2 * mp + 2) <= 16383)
+            for (int l = 0; l < kMxLevels; ++l)
+                if (mx16_level(l)) packed |= 1u << l;
+    }
+    ctx_set_matrix_packed(ctx, packed);
     if (n_pairs == 0) return LOGAN_OK;
     if (!seeds || !out || !workspace || n_pairs > 0x7fffffffu) return LOGAN_EINVAL;
     if (reinterpret_cast<uintptr_t>(workspace) % 256) return LOGAN_EINVAL;
@@ -833,7 +1228,7 @@ extern "C" int logan_extend_batch_matrix(logan_ctx_t* ctx, const logan_seqs_t* s
                     X_per_pair, items, info, ext, queue, qcap, counters);
                 e = cudaGetLastError();
                 if (e == cudaSuccess) {
-                    MxArgs a;
+                    MxArgs a{};
                     a.pa = pa.bases;
                     a.pb = pb.bases;
                     a.items = items;
@@ -854,8 +1249,12 @@ extern "C" int logan_extend_batch_matrix(logan_ctx_t* ctx, const logan_seqs_t* s
                     a.cells_level = kMxRingQueue;
                     // register windows of 64 .. 512 rows, narrowest first,
                     // then the ring for what outgrew them
+                    a.sub_min = sub_min;
+                    a.one = 1;
                     for (int l = 0; l < kMxLevels && e == cudaSuccess; ++l)
-                        e = launch_mx_level(l, a, sms * mx_level_blocks(l), s);
+                        e = ((packed >> l) & 1u)
+                                ? launch_mx16_level(l, a, sms * mx16_level_blocks(l), s)
+                                : launch_mx_level(l, a, sms * mx_level_blocks(l), s);
                     if (e == cudaSuccess) {
                         k_mx_ring<true><<<L.slots, kMxThreads, 0, s>>>(a);
                         e = cudaGetLastError();

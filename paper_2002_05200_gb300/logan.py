@@ -22,7 +22,7 @@ EINVAL, ENOMEM, EAGAIN, ECUDA, ETIMEOUT, ECANCELED, ERANGE, ENOTFOUND = \
     -22, -12, -11, -5, -110, -125, -34, -2
 OPT_GRAPHS, OPT_TIMING, OPT_FORCE_LEVEL, OPT_MAX_LEVEL, OPT_RING_CAP, OPT_PLAIN_LEVEL = 1, 2, 3, 4, 5, 6
 OPT_DEVICE, OPT_MIGRATION_MB, OPT_CONCURRENT, OPT_LONG_ITEM, OPT_PACKED16 = 7, 8, 9, 10, 11
-OPT_AFFINE_PACKED = 12
+OPT_AFFINE_PACKED, OPT_MATRIX_PACKED = 12, 13
 X_CLASSES = 8
 
 RESULT_DTYPE = np.dtype([("score", "<i4"), ("left", "<i4"), ("right", "<i4"), ("status", "<i4"),

@@ -127,3 +127,36 @@ def test_band_beyond_the_ring_reports_erange(ctx):
     assert g["status"][0] == logan.ERANGE
     ref = oracle.run_batch_matrix(b.subset(np.arange(1, 7)), M, -11, -1)[0]
     assert_same(g[1:], ref, "the other pairs")
+
+
+@pytest.mark.parametrize("go,ge,X", [(-11, -1, 60), (-5, -2, 100), (0, -4, 30)])
+def test_packed_windows_equal_32bit_and_oracle(ctx, go, ge, X):
+    # the packed windows (128, 256, 512 rows: two cells per register, the
+    # table as 16-bit entries) and the 32-bit ones give the oracle's results;
+    # the call reports which windows ran packed
+    b = synth.protein_pairs(500, lo=50, hi=2000, seed=21)
+    b.X = X
+    M = synth.BLOSUM62
+    ref = oracle.run_batch_matrix(b, M, go, ge)[0]
+    try:
+        ctx.set_option(logan.OPT_PACKED16, 1)
+        g16 = run_matrix(ctx, b, M, go, ge)
+        packed = ctx.get_option(logan.OPT_MATRIX_PACKED)
+        ctx.set_option(logan.OPT_PACKED16, 0)
+        g32 = run_matrix(ctx, b, M, go, ge)
+        assert ctx.get_option(logan.OPT_MATRIX_PACKED) == 0
+    finally:
+        ctx.set_option(logan.OPT_PACKED16, 1)
+    assert packed == 0b1110, packed
+    assert_same(g16, ref, f"packed {go},{ge},{X}")
+    assert_same(g32, ref, f"32-bit {go},{ge},{X}")
+
+
+def test_packed_windows_bounds(ctx):
+    # a matrix whose range does not fit 16-bit keys keeps the 32-bit windows
+    rng = np.random.default_rng(23)
+    M = rng.integers(-900, 901, size=(20, 20)).astype(np.int32)
+    b = synth.protein_pairs(60, lo=30, hi=300, seed=24)
+    g = run_matrix(ctx, b, M, -50, -10)
+    assert ctx.get_option(logan.OPT_MATRIX_PACKED) == 0
+    assert_same(g, oracle.run_batch_matrix(b, M, -50, -10)[0], "wide matrix")
