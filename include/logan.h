@@ -180,7 +180,9 @@ int logan_extend_batch_plain(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  * Per pair, max(|match|, |mismatch|, |gap_open| + |gap_extend|) * (m + n)
  * + X must stay below 2^29 (else LOGAN_EINVAL for the pair).  Bands are
  * held in register windows of 64, 128, 256 and 512 rows (the first by X:
- * <= 35, <= 150, <= 300, larger); a band that outgrows 512 rows, or an X
+ * <= 35, <= 150, <= 300, larger; the last three two cells to a 32-bit
+ * register when the scores fit 16 bits, LOGAN_OPT_PACKED16 and
+ * LOGAN_OPT_AFFINE_PACKED); a band that outgrows 512 rows, or an X
  * above 2^20 - 4096, continues in the workspace's device-memory ring
  * (2^LOGAN_OPT_RING_CAP rows: 65,536 by default); only a band of 65,536 rows
  * or more (2^LOGAN_OPT_RING_CAP) gets status LOGAN_ERANGE.  Runs on
@@ -214,9 +216,14 @@ int logan_extend_batch_affine(logan_ctx_t *ctx, const logan_seqs_t *seqsA,
  *   workspace: device, 256-byte aligned, at least
  *       logan_matrix_workspace_size bytes; caller-owned.
  * Per pair, max(max|entry|, |gap_open| + |gap_extend|) * (m + n) + X must
- * stay below 2^29 (else LOGAN_EINVAL for the pair).  Every extension runs in
- * one block of 256 threads over a device-memory ring of
- * 2^LOGAN_MATRIX_RING_LOG2 rows; a wider band gets LOGAN_ERANGE.  Returns
+ * stay below 2^29 (else LOGAN_EINVAL for the pair).  Extensions start in
+ * register windows of 64 rows and move to 128, 256 and 512 rows as their
+ * bands outgrow them (restarting; with a scalar X the three wider windows
+ * run two cells to a 32-bit register when the matrix's range and X fit
+ * 16 bits, LOGAN_OPT_PACKED16 and LOGAN_OPT_MATRIX_PACKED); a band wider
+ * than 512 rows, or an X above 2^20 - 4096, continues in one block of 256
+ * threads over a device-memory ring of 2^LOGAN_MATRIX_RING_LOG2 rows, and a
+ * band wider than that gets LOGAN_ERANGE.  Returns
  * LOGAN_EINVAL for invalid scalars or pointers (K outside 1..32, an entry
  * out of range, packed pools), LOGAN_ENOMEM if ws_bytes is too small,
  * LOGAN_ECUDA on a launch failure.
