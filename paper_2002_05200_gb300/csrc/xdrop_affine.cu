@@ -37,7 +37,6 @@ struct AGroup {
     static constexpr int W = G * C;
     static constexpr int LOG2W = W == 64 ? 6 : W == 128 ? 7 : W == 256 ? 8 : W == 512 ? 9 : 10;
     static constexpr uint32_t MASK2C = (C >= 16) ? 0xffffffffu : ((1u << (2 * C)) - 1u);
-    static constexpr uint32_t ALLC = (C >= 32) ? 0xffffffffu : ((1u << C) - 1u);
     static constexpr int PREFETCH = 16 * G;  // b' codes held by a unit
     static constexpr int UNROLL = 3;         // steps per loop iteration
     static_assert(C <= 16 && C % 2 == 0, "a lane's row codes fit one word");

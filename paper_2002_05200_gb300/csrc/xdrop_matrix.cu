@@ -237,7 +237,6 @@ template <int G, int C>
 struct MGroup {
     static constexpr int W = G * C;
     static constexpr int LOG2W = W == 64 ? 6 : W == 128 ? 7 : W == 256 ? 8 : 9;
-    static constexpr int NW = C / 4;        // letter words per lane
     static constexpr int PREFETCH = 4 * G;  // b' letters a unit holds
     static_assert(C % 4 == 0 && (1 << LOG2W) == W, "shape");
 };
