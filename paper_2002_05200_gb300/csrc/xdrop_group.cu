@@ -16,7 +16,12 @@
 // u = S - T_d with T_d = best_{<d} - X, so a cell is live iff u >= 0 and -inf
 // is NEGU.  Moving a value from d-1 or d-2 to d adds T_{d-1} - T_d or
 // T_{d-2} - T_d; both are folded into the per-step gap and match/mismatch
-// constants, so re-basing costs nothing per cell.  Every live cell's
+// constants, so re-basing costs nothing per cell.  (The one-warp forms,
+// G = 32 with C < 32, hold anti-diagonal d relative to T_{d-1} instead and
+// prune against T_d - T_{d-1}: the same values shifted by a constant, with
+// the same cost per cell, but a step's additions and maxima no longer wait
+// for the previous step's reductions -- what a lone long extension waits
+// on.)  Every live cell's
 // key = u*W + (W-1-row) is reduced by one max per unit: the largest key holds
 // the anti-diagonal's best score and, for equal scores, the smallest row --
 // the best cell's tie-break without a second search.  Live rows are one warp
@@ -62,6 +67,9 @@ struct Group {
     static constexpr Code MASK2C = (C >= 16) ? ~Code(0) : ((Code(1) << (2 * C)) - 1u);
     static constexpr uint32_t ALLC = (C >= 32) ? 0xffffffffu : ((1u << C) - 1u);
     static constexpr int PREFETCH = 16 * G;  // b' codes held by a unit
+    // one extension per warp (G = 32) with C < 32: each anti-diagonal is
+    // stored relative to the threshold of the one before it (see group_step)
+    static constexpr bool LAT = G == 32 && C < 32;
     static_assert((1 << LOG2W) == W, "window must be a power of two");
 };
 
@@ -70,6 +78,7 @@ template <int C>
 struct UState {
     int base, lo, hi, d;
     int best, T, T1, T2;  // T = T_d for the coming step, T1 = T_{d-1}, T2 = T_{d-2}
+    int R1, R2;           // one-warp forms: the thresholds the d-1 / d-2 values are relative to
     int bi, bj;
     int m, n, X;
     unsigned long long cells;
@@ -140,6 +149,8 @@ __device__ __forceinline__ void unit_init(const KernelArgs& ka, UState<C>& u, ui
         u.T = rec[MIG_T];
         u.T1 = rec[MIG_T1];
         u.T2 = rec[MIG_T2];
+        u.R1 = u.T1;  // a record holds d-1 relative to T_{d-1}, d-2 relative to T_{d-2}
+        u.R2 = u.T2;
         u.bi = rec[MIG_BI];
         u.bj = rec[MIG_BJ];
         u.cells = (unsigned long long)uint32_t(rec[MIG_CELLS_LO]) |
@@ -166,6 +177,8 @@ __device__ __forceinline__ void unit_init(const KernelArgs& ka, UState<C>& u, ui
         u.T = -it.X;
         u.T1 = -it.X;
         u.T2 = -it.X;
+        u.R1 = -it.X;
+        u.R2 = -it.X;
         u.bi = 0;
         u.bj = 0;
         u.cells = 0ull;
@@ -250,10 +263,18 @@ __device__ __forceinline__ void unit_prepare(const KernelArgs& ka, UState<C>& u,
             slot = __shfl_sync(FULL, slot, unit * G);
             if (ovf && slot >= 0) {
                 int32_t* rec = mig_record(ka, slot);
+                // (records hold d-1 relative to T_{d-1} and d-2 relative to
+                // T_{d-2}; the one-warp forms re-base their values)
 #pragma unroll
                 for (int k = 0; k < C; ++k) {
-                    rec[kMigHeader + gl * C + k] = Q1[k];
-                    rec[kMigHeader + Gr::W + gl * C + k] = Q2[k];
+                    if constexpr (Gr::LAT) {
+                        rec[kMigHeader + gl * C + k] = Q1[k] >= 0 ? Q1[k] + (u.R1 - u.T1) : NEGU;
+                        rec[kMigHeader + Gr::W + gl * C + k] =
+                            Q2[k] >= 0 ? Q2[k] + (u.R2 - u.T2) : NEGU;
+                    } else {
+                        rec[kMigHeader + gl * C + k] = Q1[k];
+                        rec[kMigHeader + Gr::W + gl * C + k] = Q2[k];
+                    }
                 }
                 if (gl == 0) {
                     rec[MIG_KIND] = MIG_RELATIVE;
@@ -318,9 +339,14 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
     const typename Gr::Code eq = ~(x | (x >> 1));  // bit 2k set iff row k's bases match
     const uint32_t eq_lo = uint32_t(eq);
     const uint32_t eq_hi = uint32_t(uint64_t(eq) >> 32);  // rows 16..31 (C = 32 only)
-    // per-step constants: re-basing of d-1 and d-2 values onto T_d
-    const int o1 = ka.sc.gap + u.T1 - u.T;
-    const int o2 = u.T2 - u.T;
+    // per-step constants: re-basing of d-1 and d-2 values onto T_d; in the
+    // one-warp forms onto T_{d-1} instead (d-1 and d-2 are held relative to
+    // R1 = T_{d-2} and R2 = T_{d-3}), so that nothing before the prune waits
+    // for the previous anti-diagonal's reductions -- the cells' additions and
+    // maxima overlap them -- and a cell is live iff its value >= T_d - T_{d-1}
+    const int o1 = Gr::LAT ? ka.sc.gap + u.R1 - u.T1 : ka.sc.gap + u.T1 - u.T;
+    const int o2 = Gr::LAT ? u.R2 - u.T1 : u.T2 - u.T;
+    const int dT = Gr::LAT ? u.T - u.T1 : 0;
     const int sMM = ka.sc.mismatch + o2;
     const int dsub = ka.sc.mismatch - ka.sc.match;  // added back once per match (as -1 * dsub)
     // rows of this lane inside [rlo, rhi]: bits [k0, k1) of rb
@@ -374,7 +400,7 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
             int v = __vimax3_s32(gp, g, t);
             gp = g;
             const bool inr = (rb & (1u << kk)) != 0u;
-            v = (inr & (v >= 0)) ? v : NEGU;
+            v = (inr & (v >= dT)) ? v : NEGU;
             O[kk] = v;
             key[h] = v * wscale + (C - 1 - kk);
             dc[kk / RB] = __funnelshift_l(uint32_t(v), dc[kk / RB], 1);
@@ -439,16 +465,29 @@ __device__ __forceinline__ void group_step(const KernelArgs& ka, UState<C>& u, i
     }
     const bool adv = run && rlast >= 0;
     const int umax = wkey >> Gr::LOG2W;
-    const bool imp = adv && umax > u.X;  // S > best  <=>  S - T_d > X
+    // S > best  <=>  S - T_d > X (one-warp forms: S - T_{d-1} > best - T_{d-1})
+    const int ref = Gr::LAT ? u.T1 : u.T;
+    const bool imp = adv && umax > (Gr::LAT ? u.best - u.T1 : u.X);
     const int r = Gr::W - 1 - (wkey & (Gr::W - 1));
-    const int best = imp ? u.T + umax : u.best;
+    const int best = imp ? ref + umax : u.best;
     u.bi = imp ? u.base + r : u.bi;
     u.bj = imp ? u.d - (u.base + r) : u.bj;
     u.best = best;
     const int T = u.T, T1 = u.T1;
-    u.T2 = adv ? T1 : u.T2;
-    u.T1 = adv ? T : T1;
-    u.T = adv ? best - u.X : T;
+    if constexpr (Gr::LAT) {
+        // unconditional shifts: a step that does not advance ends the
+        // extension, after which they are never read, and the next step's
+        // offsets do not wait for the range reductions
+        u.R2 = u.R1;
+        u.R1 = T1;
+        u.T2 = T1;
+        u.T1 = T;
+        u.T = best - u.X;
+    } else {
+        u.T2 = adv ? T1 : u.T2;
+        u.T1 = adv ? T : T1;
+        u.T = adv ? best - u.X : T;
+    }
     u.lo = adv ? u.base + rfirst : u.lo;
     u.hi = adv ? u.base + rlast : u.hi;
     u.done = u.done || (u.active && !adv);
@@ -485,6 +524,7 @@ __global__ void __launch_bounds__(128, (C == 32) ? 3 : (C == 16) ? 4 : (C == 8) 
     u.base = u.lo = u.hi = 0;
     u.d = 1;
     u.T = u.T1 = u.T2 = u.best = u.bi = u.bj = 0;
+    u.R1 = u.R2 = 0;
     u.X = 0;
     u.cells = 0ull;
     u.cells0 = 0ull;
