@@ -42,3 +42,38 @@ def test_reference_other_rank_is_silent():
     lines = run(["--impl", "reference", "--pairs", "50", "--steps", "1", "--warmup", "0",
                  "--cpu-seconds", "1"], env={"RANK": "1", "WORLD_SIZE": "2"})
     assert lines == []
+
+
+def _bench_module():
+    import importlib.util
+    spec = importlib.util.spec_from_file_location("bench_under_test", os.path.join(ROOT, "bench.py"))
+    m = importlib.util.module_from_spec(spec)
+    spec.loader.exec_module(m)
+    return m
+
+
+def test_profiled_kernel_sources_match_the_capture():
+    """The traffic and mixed ceiling in the bench line come from one ncu
+    capture of the packed level-2 kernel; they are reported only while its
+    sources hash to the captured ones, and these sources are those."""
+    b = _bench_module()
+    assert b._profile_current(b.PROFILED["level"])
+    assert not b._profile_current(b.PROFILED["level"] + 1)
+    # traffic scales with the extensions a launch starts
+    t = b.profiled_traffic(b.PROFILED["level"], 2 * b.PROFILED["items"])
+    assert t == pytest.approx(2 * b.PROFILED["bytes"])
+
+
+def test_mixed_ceiling_is_the_slowest_pipe():
+    """min(alu / (1 - f), fma / f, issue): a stream with a share f of its
+    instructions on the FMA pipe, the rest on the ALU pipe, one issue port."""
+    b = _bench_module()
+    f = b.PROFILED["fma_share"]
+    assert 0.0 < f < 1.0
+    lvl = b.PROFILED["level"]
+    assert b.mixed_ceiling(lvl, 20.0, 20.0, 39.1) == pytest.approx(min(20.0 / (1 - f), 20.0 / f, 39.1))
+    # issue-bound when both pipes are fast
+    assert b.mixed_ceiling(lvl, 1e6, 1e6, 39.1) == pytest.approx(39.1)
+    # a pure ALU stream would be limited by the ALU rate alone
+    assert b.mixed_ceiling(lvl, 20.0, 1e6, 1e6) == pytest.approx(20.0 / (1 - f))
+    assert b.mixed_ceiling(lvl + 1, 20.0, 20.0, 39.1) is None
