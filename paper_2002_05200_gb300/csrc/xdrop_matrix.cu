@@ -417,6 +417,7 @@ __device__ __forceinline__ void mg_step(const MxArgs& a, const int* tab, MState&
     if (gl == 0) h1c = f1c = h2c = NEGM;
     const int T = u.best - u.X;
     const int goe = a.go + a.ge;
+    const int one = a.one;
     const int i0 = u.base + gl * C;
     const int k0 = __viaddmin_s32_relu(rlo, -i0, C);
     const int k1 = __viaddmin_s32_relu(rhi, 1 - i0, C);
@@ -429,11 +430,13 @@ __device__ __forceinline__ void mg_step(const MxArgs& a, const int* tab, MState&
         const int uh = k ? H1[k - 1] : h1c;
         const int uf = k ? F[k - 1] : f1c;
         const int dg = k ? H2[k - 1] : h2c;
-        const int e = __vimax3_s32(E[k] + a.ge, H1[k] + goe, NEGM);
-        const int f = __vimax3_s32(uf + a.ge, uh + goe, NEGM);
+        // the additions as multiply-adds with a run-time 1 (FMA pipe), the
+        // maxima 3-input DPX (ALU pipe)
+        const int e = __vimax3_s32(E[k] * one + a.ge, H1[k] * one + goe, NEGM);
+        const int f = __vimax3_s32(uf * one + a.ge, uh * one + goe, NEGM);
         const uint32_t la = (aw[k >> 2] >> (8 * (k & 3))) & 0xffu;
         const uint32_t lb = (bw[k >> 2] >> (8 * (k & 3))) & 0xffu;
-        const int h = __vimax3_s32(dg + tab[la * uint32_t(a.K) + lb], e, f);
+        const int h = __vimax3_s32(dg * one + tab[la * uint32_t(a.K) + lb], e, f);
         const bool live = ((rb >> k) & 1u) && h >= T;
         HO[k] = live ? h : NEGM;
         E[k] = live ? e : NEGM;
