@@ -193,6 +193,31 @@ def workload_config(b, name, pairs):
             "l2": l2_note(b), **common}
 
 
+METRIC_AFFINE = METRIC + " -- affine-gap path"
+METRIC_MATRIX = METRIC + " -- substitution matrix (BLOSUM62 protein)"
+
+
+def affine_config(b, name, pairs, go, ge):
+    """The affine line's config: the workload's, with the Gotoh scoring."""
+    cfg = workload_config(b, name, pairs)
+    cfg["scoring"] = {"match": b.match, "mismatch": b.mismatch, "gap_open": go, "gap_extend": ge}
+    cfg["path"] = "affine gaps (logan_extend_batch_affine)"
+    return cfg
+
+
+def matrix_config(b, go, ge):
+    """The substitution-matrix line's config (protein pairs, BLOSUM62)."""
+    small = b.pool_bases < FLUSH_BELOW
+    return {"workload": "protein_pairs", "pairs": b.n_pairs,
+            "lengths": "log-uniform 100-2000 residues", "related_frac": 0.8,
+            "edits": 0.25, "seed_len": 8, "X": b.X, "matrix": "BLOSUM62",
+            "gap_open": go, "gap_extend": ge, "input": "letter codes, one byte each",
+            "parallelism": "replicas (independent pairs per GPU, no collective)",
+            "l2": (f"letter pools {b.pool_bases / 1e6:.0f} MB: L2 flushed (512 MB write) "
+                   "before every timed step, outside its events") if small else
+                  f"letter pools {b.pool_bases / 1e6:.0f} MB, larger than L2: no flush"}
+
+
 def measured_hbm_gbs():
     """The machine's measured HBM copy bandwidth, when the peaks file is present."""
     try:
@@ -467,16 +492,19 @@ def serving_run(ctx, lib, lib_res, rate: float, budget_gb: float, inflight: int,
 
 
 # ---------------------------------------------------------------- CPU oracle
-def cpu_sample(b, seconds: float, threads=None):
+def cpu_sample(b, seconds: float, threads=None, run=None):
     """Times the oracle on consecutive chunks of pairs until `seconds` of host
-    time are spent (at least one chunk).  Returns (GCUPS, cores, pairs, cells, s)."""
+    time are spent (at least one chunk).  `run(batch, threads)` is the oracle
+    call (default: the linear extension).  Returns (GCUPS, cores, pairs,
+    cells, s)."""
     import oracle
     threads = threads or os.cpu_count() or 1
+    run = run or oracle.run_batch
     chunk = max(threads * 4, 64)
     done, cells, t0 = 0, 0, time.perf_counter()
     while done < b.n_pairs:
         sub = b.subset(np.arange(done, min(done + chunk, b.n_pairs)))
-        res, used = oracle.run_batch(sub, threads)
+        res, used = run(sub, threads)
         cells += int(res["cells"][res["status"] == 0].sum())
         done += sub.n_pairs
         if time.perf_counter() - t0 >= seconds:
@@ -486,25 +514,47 @@ def cpu_sample(b, seconds: float, threads=None):
 
 
 def run_reference(args, rank, world):
+    """The oracle on the host cores, on the line the GPU arm prints for the
+    same arguments (linear, affine with --gap-open, matrix with --matrix)."""
     if rank != 0:
         return
-    b = workload(args.workload, args.pairs, 0)
+    import oracle
+    if args.matrix:
+        from paper_2002_05200_gb300 import synth
+        go = args.gap_open if args.gap_open is not None else -11
+        ge = args.gap_extend
+        b = synth.protein_pairs(args.pairs, seed=12)
+        metric, cfg, what = METRIC_MATRIX, matrix_config(b, go, ge), "matrix oracle"
+
+        def run(sub, threads):
+            return oracle.run_batch_matrix(sub, synth.BLOSUM62, go, ge, threads)
+    elif args.gap_open is not None:
+        go, ge = args.gap_open, args.gap_extend
+        b = workload(args.workload, args.pairs, 0)
+        metric, cfg = METRIC_AFFINE, affine_config(b, args.workload, args.pairs, go, ge)
+        what = "affine oracle"
+
+        def run(sub, threads):
+            return oracle.run_batch_affine(sub, go, ge, threads)
+    else:
+        b = workload(args.workload, args.pairs, 0)
+        metric, cfg, what, run = METRIC, workload_config(b, args.workload, args.pairs), "oracle", None
     per_step = max(1.0, min(args.cpu_seconds, 150.0 / max(1, args.steps + args.warmup)))
     for _ in range(args.warmup):
-        cpu_sample(b, per_step / 4)
+        cpu_sample(b, per_step / 4, run=run)
     vals, cores, pairs, secs = [], 0, 0, 0.0
     for _ in range(args.steps):
-        g, cores, pairs, cells, dt = cpu_sample(b, per_step)
+        g, cores, pairs, cells, dt = cpu_sample(b, per_step, run=run)
         vals.append(g)
         secs += dt
     value = float(np.mean(vals))
     sample = (f"first {pairs} of {b.n_pairs} pairs per step (~{per_step:.0f} s of host time), "
-              "all host cores, one pair per task")
-    line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "GCUPS",
+              f"{what}, all host cores, one pair per task")
+    line = {"impl": "reference", "metric": metric, "value": value, "unit": "GCUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
             "ms_per_step": secs / args.steps * 1e3, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": "int64", "data": "synthetic",
-            "config": workload_config(b, args.workload, args.pairs),
+            "config": cfg,
             "cpu_baseline": {"value": value, "unit": "GCUPS", "cores": cores, "kind": "oracle",
                              "sample": sample},
             "e2e": {"value": value, "unit": "GCUPS", "h2d_bytes_per_step": 0,
@@ -643,10 +693,8 @@ def affine_main(args, b, A, B, S, Xs, ctx, ws, out, stream, timed, rank, world, 
     # levels, ring, combine
     launches = n_pools + (0 if packed else n_pools) + 1 + 3 + 4 + 1 + 1
     affine_packed = int(ctx.get_option(logan.OPT_AFFINE_PACKED))
-    cfg = workload_config(b, args.workload, args.pairs)
-    cfg["scoring"] = {"match": b.match, "mismatch": b.mismatch, "gap_open": go, "gap_extend": ge}
-    cfg["path"] = "affine gaps (logan_extend_batch_affine)"
-    line = {"metric": METRIC + " -- affine-gap path", "value": value, "unit": "GCUPS",
+    cfg = affine_config(b, args.workload, args.pairs, go, ge)
+    line = {"metric": METRIC_AFFINE, "value": value, "unit": "GCUPS",
             "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
             # the packed windows compute in 16-bit halves where the bound holds
@@ -779,7 +827,7 @@ def matrix_main(args, rank, world, local):
     peak = logan.intpeak(local, 1, 2000)[0] / 1e9
     achieved = OPS_PER_CELL_AFFINE * cells / (ms * 1e-3) / 1e9
     matrix_packed = int(ctx.get_option(logan.OPT_MATRIX_PACKED))
-    line = {"metric": METRIC + " -- substitution matrix (BLOSUM62 protein)",
+    line = {"metric": METRIC_MATRIX,
             "value": tot / (ms * 1e-3) / 1e9, "unit": "GCUPS", "n_gpus": world,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
@@ -787,14 +835,7 @@ def matrix_main(args, rank, world, local):
             "dtype": "int16x2+int32" if matrix_packed else "int32",
             "matrix_packed_levels": [l for l in range(4) if (matrix_packed >> l) & 1],
             "data": "synthetic",
-            "config": {"workload": "protein_pairs", "pairs": b.n_pairs,
-                       "lengths": "log-uniform 100-2000 residues", "related_frac": 0.8,
-                       "edits": 0.25, "seed_len": 8, "X": b.X, "matrix": "BLOSUM62",
-                       "gap_open": go, "gap_extend": ge, "input": "letter codes, one byte each",
-                       "parallelism": "replicas (independent pairs per GPU, no collective)",
-                       "l2": (f"letter pools {b.pool_bases / 1e6:.0f} MB: L2 flushed (512 MB write) "
-                              "before every timed step, outside its events") if small else
-                             f"letter pools {b.pool_bases / 1e6:.0f} MB, larger than L2: no flush"},
+            "config": matrix_config(b, go, ge),
             # reset, validate A and B, split, four register levels, ring, combine
             "clocks": clk.summary(), "gpu_launches": 10 * args.steps, "cells_per_step": tot,
             "erange_pairs": int((res["status"] == logan.ERANGE).sum()),

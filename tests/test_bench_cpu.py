@@ -77,3 +77,19 @@ def test_mixed_ceiling_is_the_slowest_pipe():
     # a pure ALU stream would be limited by the ALU rate alone
     assert b.mixed_ceiling(lvl, 20.0, 1e6, 1e6) == pytest.approx(20.0 / (1 - f))
     assert b.mixed_ceiling(lvl + 1, 20.0, 20.0, 39.1) is None
+
+
+@pytest.mark.parametrize("flags,metric_tail,cfg_key", [
+    (["--gap-open", "-2", "--gap-extend", "-1"], "affine-gap path", "path"),
+    (["--matrix", "blosum62"], "substitution matrix (BLOSUM62 protein)", "matrix"),
+])
+def test_reference_line_other_paths(flags, metric_tail, cfg_key):
+    """--impl reference times the oracle of the path the GPU arm runs for the
+    same flags, under that arm's metric and config."""
+    lines = run(["--impl", "reference", *flags, "--pairs", "100", "--steps", "1",
+                 "--warmup", "0", "--cpu-seconds", "1"])
+    assert len(lines) == 1
+    j = lines[0]
+    assert j["metric"].endswith(metric_tail) and j["value"] > 0
+    assert cfg_key in j["config"] and "l2" in j["config"]
+    assert j["cpu_baseline"]["value"] == j["value"]
